@@ -1,0 +1,181 @@
+/*
+ * cryptoemu.h — C ABI of the GB300 TFHE gate-bootstrapping library.
+ *
+ * The library evaluates the bootstrapped binary gates on which the paper's
+ * homomorphic functional units are built (§3 "TFHE Library", Table "TFHE API
+ * Benchmark": NAND, OR, AND, XOR, XNOR, NOR, ANDNY, ANDYN, ORNY, ORYN and
+ * MUX; one bootstrap per binary gate, two for MUX).  A gate is four steps:
+ * the linear LWE combination, the modulus switch to 2N, blind rotation
+ * (n = 500 CMux external products over Z_{2^32}[X]/(X^1024 + 1)) and sample
+ * extraction followed by LWE key switching.  The client side (keygen, encrypt,
+ * decrypt) follows the paper's cloud service model (§4, "Cloud service
+ * model"): the secret key stays in memory the client owns; the cloud key
+ * (bootstrapping + key-switching key) is handed to a context that keeps it
+ * resident on the GPU.
+ *
+ * Parameters (fixed): LWE n = 500, sigma = 2^-15; TRLWE N = 1024, k = 1;
+ * gadget l = 3, Bg = 2^10, sigma_bk = 9e-9; key switch t = 8, base 2^2.
+ * Torus values are uint32 (x <-> x / 2^32); a bit is encoded as +1/8 (true)
+ * or -1/8 (false).  All GPU arithmetic is exact integer arithmetic, so every
+ * result is bit-identical to the plain CPU definition of the same step.
+ *
+ * Conventions for every call:
+ *  - Returns a ce_status (0 = success); nothing aborts the process.  On error
+ *    ce_last_error() returns a message for the calling thread.
+ *  - Host buffers are owned by the caller and only read/written during the
+ *    call.  Device buffers ("_device" calls) are owned by the caller, must
+ *    live on the context's device and stay valid until the work enqueued on
+ *    the given stream has finished; those calls are asynchronous.
+ *  - Everything the context allocates on the device (keys, scratch) is owned
+ *    by the context and released by ce_destroy / ce_client_evict.
+ *  - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef CRYPTOEMU_H
+#define CRYPTOEMU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CE_LWE_N 500          /* LWE dimension n */
+#define CE_LWE_WORDS 501      /* words of one LWE ciphertext: a[500], b */
+#define CE_RING_N 1024        /* TRLWE ring degree N */
+#define CE_BSK_WORDS (500u * 6u * 2u * 1024u)        /* 3,072,000 uint32 */
+#define CE_KSK_WORDS (1024u * 8u * 4u * 501u)        /* 16,416,768 uint32 */
+
+typedef enum {
+    CE_OK = 0,
+    CE_EINVAL = -1,     /* bad argument (null pointer, size, opcode, id) */
+    CE_ENOMEM = -2,     /* host or device allocation failed */
+    CE_EADMIT = -3,     /* client refused: over the context's HBM budget */
+    CE_ETIMEOUT = -4,   /* a bounded device-side wait or a timeout expired */
+    CE_ECUDA = -5,      /* CUDA runtime error (no device, launch failure, ...) */
+    CE_ENOTFOUND = -6   /* unknown client id */
+} ce_status;
+
+/* Bootstrapped binary gates (truth tables: §3, Table "TFHE API Benchmark").
+ * ANDNY(a,b) = (NOT a) AND b, ANDYN(a,b) = a AND (NOT b), ORNY, ORYN alike. */
+typedef enum {
+    CE_NAND = 0, CE_AND = 1, CE_OR = 2, CE_XOR = 3, CE_NOR = 4, CE_XNOR = 5,
+    CE_ANDNY = 6, CE_ANDYN = 7, CE_ORNY = 8, CE_ORYN = 9
+} ce_gate_op;
+
+/* One LWE ciphertext: 2004 bytes, a[0..499] then b. */
+typedef struct { uint32_t a[CE_LWE_N]; uint32_t b; } ce_lwe;
+
+typedef struct ce_ctx ce_ctx;
+
+/* ------------------------------------------------------------- client --- */
+
+/* Secret key bytes: "CESK" magic (4 B), version (uint32 = 1), then the LWE key
+ * s[500] and the TRLWE key K[1024] as uint32 values in {0,1}.  Each bit is the
+ * top bit of one uniform draw of the counter-based SplitMix64 stream
+ * described in ce_cloud_keygen.  The buffer is allocated by the library and
+ * freed with ce_free. */
+#define CE_SECRET_BYTES (8u + 4u * (500u + 1024u))
+ce_status ce_secret_keygen(uint64_t seed, void **secret_out, size_t *bytes_out);
+
+/* Cloud key bytes: "CECK" magic, version (uint32 = 1), then the bootstrapping
+ * key BSK[i][r][comp][j] (i < 500 key bits, r = c*3 + (p-1) TRGSW rows with
+ * c = 0 a-part / 1 b-part and p = 1..3 gadget levels, comp 0 = a / 1 = b,
+ * j < 1024 coefficients; each row a TRLWE encryption of zero under K with
+ * s_i * 2^(32 - 10 p) added to the constant coefficient of component c), then
+ * the key-switching key KSK[j][q][v][m] (j < 1024, q < 8, v < 4, m <= 500; an
+ * LWE encryption under s of v * K_j * 2^(32 - 2 (q+1)); v = 0 rows stored).
+ * Randomness: uniform draw i of domain d is the high half of SplitMix64
+ * output d * 2^40 + i for the given seed; Gaussian noise i uses draws 2i and
+ * 2i+1 through Box-Muller (domains: 3 BSK a, 4 BSK noise, 5 KSK a, 6 KSK
+ * noise).  Allocated by the library (about 78 MB), freed with ce_free.
+ * The TRGSW construction is the one of the TFHE papers cited in §2/§3. */
+#define CE_CLOUD_BYTES (8ull + 4ull * ((unsigned long long)CE_BSK_WORDS + CE_KSK_WORDS))
+ce_status ce_cloud_keygen(const void *secret, uint64_t seed, void **cloud_out,
+                          size_t *bytes_out);
+void ce_free(void *p);
+
+/* Encrypt one bit: a[m] = uniform draw ctr*500 + m of domain 7, b = <a,s> +
+ * e + (bit ? +1/8 : -1/8), e = Gaussian draw ctr of domain 8 (sigma 2^-15).
+ * (§3, Table "TFHE API Benchmark": Encrypt.) */
+ce_status ce_encrypt_bit(const void *secret, int bit, uint64_t seed,
+                         uint64_t ctr, ce_lwe *out);
+/* Decrypt: returns 1 if b - <a,s> read as a signed 32-bit value is > 0, 0
+ * otherwise, or a negative ce_status on a bad argument.  (§3: Decrypt.) */
+int ce_decrypt_bit(const void *secret, const ce_lwe *c);
+
+/* ------------------------------------------------------------- context --- */
+
+/* Create a context on CUDA device `device`.  `hbm_budget_bytes` caps the
+ * device memory the context's clients may hold (0 = 90% of the free memory
+ * at creation).  `cuda_stream` (a cudaStream_t, may be NULL for the legacy
+ * default stream) is the stream all synchronous calls enqueue on. */
+ce_status ce_create(ce_ctx **out, int device, uint64_t hbm_budget_bytes,
+                    void *cuda_stream);
+void ce_destroy(ce_ctx *ctx);
+const char *ce_last_error(void);
+
+/* Admit a client: copies its cloud key (CE_CLOUD_BYTES host bytes) to the
+ * device and converts the bootstrapping key to the negacyclic-transform
+ * domain used by the blind-rotation kernel (98,304 B per key bit).  Returns
+ * CE_EADMIT when the client's device footprint would exceed the budget. */
+ce_status ce_client_admit(ce_ctx *ctx, const void *cloud_key, size_t bytes,
+                          int *client_id);
+ce_status ce_client_evict(ce_ctx *ctx, int client_id);
+/* Device bytes a client holds (keys + register file). */
+uint64_t ce_client_footprint_bytes(void);
+
+/* ---------------------------------------------------------------- gates --- */
+
+/* One bootstrapped gate out = op(a, b) with host ciphertexts (blocking). */
+ce_status ce_gate(ce_ctx *ctx, int client, ce_gate_op op, const ce_lwe *a,
+                  const ce_lwe *b, ce_lwe *out);
+/* n independent gates out[i] = ops[i](a[i], b[i]) with host buffers: copies
+ * the inputs to the device, runs the batched path and copies the results
+ * back (blocking).  ops: n bytes (ce_gate_op values). */
+ce_status ce_gates_batch(ce_ctx *ctx, int client, const uint8_t *ops,
+                         const ce_lwe *a, const ce_lwe *b, ce_lwe *out, size_t n);
+/* Same on device buffers (d_ops: n bytes; d_a, d_b, d_out: n x 501 uint32,
+ * packed), enqueued on `cuda_stream` (NULL = the context's stream) without
+ * host synchronisation.  Steps: linear combination + modulus switch, blind
+ * rotation (one persistent launch for all n gates, bootstrapping key staged
+ * through shared memory and shared by the gates of a block), fused sample
+ * extraction + key switching.  Scratch (10 KB per gate) is owned by the
+ * context and grows on demand. */
+ce_status ce_gates_batch_device(ce_ctx *ctx, int client, const uint8_t *d_ops,
+                                const uint32_t *d_a, const uint32_t *d_b,
+                                uint32_t *d_out, size_t n, void *cuda_stream);
+
+/* n MUX gates out[i] = a[i] ? b[i] : c[i] on device buffers (two bootstraps
+ * without key switching and one key switch per MUX; §3: MUX is bootstrapped
+ * twice). */
+ce_status ce_mux_batch_device(ce_ctx *ctx, int client, const uint32_t *d_a,
+                              const uint32_t *d_b, const uint32_t *d_c,
+                              uint32_t *d_out, size_t n, void *cuda_stream);
+
+/* Building block of the blind rotation, exposed for verification: n exact
+ * negacyclic products out[i] = d[i] * k[i] in Z_{2^32}[X]/(X^1024 + 1), d a
+ * polynomial of signed 16-bit coefficients, k of uint32 coefficients, through
+ * the same 1024-point transform over p = 2^64 - 2^32 + 1 the blind rotation
+ * uses (exact because |sum| < 1024 * 2^15 * 2^32 < p / 2).  Device buffers
+ * d_d (n x 1024 int16), d_k, d_out (n x 1024 uint32); asynchronous. */
+ce_status ce_negacyclic_mul_device(ce_ctx *ctx, const int16_t *d_d,
+                                   const uint32_t *d_k, uint32_t *d_out,
+                                   size_t n, void *cuda_stream);
+
+/* Tuning of the blind-rotation launch: gates per block (1, 2 or 4) and
+ * resident blocks per SM; 0 = autotuned choice.  Applies to later calls. */
+ce_status ce_set_blind_rotate_config(ce_ctx *ctx, int gates_per_block,
+                                     int blocks_per_sm);
+/* Waits for the context's stream and reports a device-side failure of the
+ * asynchronous calls since the previous check (CE_ETIMEOUT when a bounded
+ * device wait expired). */
+ce_status ce_synchronize(ce_ctx *ctx);
+/* Number of kernels the last ce_gates_batch[_device] / ce_mux_batch_device
+ * call launched (for launch accounting). */
+int ce_last_launch_count(ce_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,277 @@
+"""ctypes binding of libcryptoemu.so (argument marshalling only).
+
+Every function keeps the name of the C entry point it wraps (see
+include/cryptoemu.h).  Host buffers are numpy arrays; device buffers are
+torch CUDA tensors (or raw device addresses as ints); streams are
+``torch.cuda.Stream`` objects, raw ``cudaStream_t`` ints, or None for the
+context's stream.  All computation happens inside the library: if the shared
+library is missing this module raises instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+LWE_N = 500
+LWE_WORDS = 501
+RING_N = 1024
+GATES = ["NAND", "AND", "OR", "XOR", "NOR", "XNOR", "ANDNY", "ANDYN", "ORNY", "ORYN"]
+GATE_ID = {g: i for i, g in enumerate(GATES)}
+
+STATUS = {0: "CE_OK", -1: "CE_EINVAL", -2: "CE_ENOMEM", -3: "CE_EADMIT", -4: "CE_ETIMEOUT",
+          -5: "CE_ECUDA", -6: "CE_ENOTFOUND"}
+
+
+class CeError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_L = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load the library (it must have been built: ``__graft_entry__.build()``)."""
+    global _L
+    if _L is not None:
+        return _L
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"{_build.LIB} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(_build.LIB)
+    vp, sz, u64, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_int
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "ce_secret_keygen": (i32, [u64, pp, ctypes.POINTER(sz)]),
+        "ce_cloud_keygen": (i32, [vp, u64, pp, ctypes.POINTER(sz)]),
+        "ce_free": (None, [vp]),
+        "ce_encrypt_bit": (i32, [vp, i32, u64, u64, vp]),
+        "ce_decrypt_bit": (i32, [vp, vp]),
+        "ce_create": (i32, [pp, i32, u64, vp]),
+        "ce_destroy": (None, [vp]),
+        "ce_last_error": (ctypes.c_char_p, []),
+        "ce_client_admit": (i32, [vp, vp, sz, ctypes.POINTER(i32)]),
+        "ce_client_evict": (i32, [vp, i32]),
+        "ce_client_footprint_bytes": (u64, []),
+        "ce_gate": (i32, [vp, i32, i32, vp, vp, vp]),
+        "ce_gates_batch": (i32, [vp, i32, vp, vp, vp, vp, sz]),
+        "ce_gates_batch_device": (i32, [vp, i32, vp, vp, vp, vp, sz, vp]),
+        "ce_mux_batch_device": (i32, [vp, i32, vp, vp, vp, vp, sz, vp]),
+        "ce_negacyclic_mul_device": (i32, [vp, vp, vp, vp, sz, vp]),
+        "ce_set_blind_rotate_config": (i32, [vp, i32, i32]),
+        "ce_last_launch_count": (i32, [vp]),
+        "ce_synchronize": (i32, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _L = L
+    return L
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/cryptoemu.h."""
+    hdr = os.path.join(os.path.dirname(_build.HERE), "include", "cryptoemu.h")
+    text = open(hdr).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ce_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise CeError(code, where, (lib().ce_last_error() or b"").decode())
+
+
+def _addr(x) -> int | None:
+    """Device address of a torch tensor / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def _host(a, dtype=np.uint32) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# ------------------------------------------------------------- client ---
+class SecretKey:
+    def __init__(self, ptr: int, nbytes: int):
+        self.ptr, self.nbytes = ptr, nbytes
+
+    def words(self) -> np.ndarray:
+        return np.ctypeslib.as_array((ctypes.c_uint32 * (self.nbytes // 4)).from_address(self.ptr))
+
+    @property
+    def s(self) -> np.ndarray:
+        return self.words()[2:2 + LWE_N].copy()
+
+    @property
+    def K(self) -> np.ndarray:
+        return self.words()[2 + LWE_N:2 + LWE_N + RING_N].copy()
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _L is not None:
+            _L.ce_free(self.ptr)
+            self.ptr = None
+
+
+class CloudKey:
+    def __init__(self, ptr: int, nbytes: int):
+        self.ptr, self.nbytes = ptr, nbytes
+
+    def words(self) -> np.ndarray:
+        return np.ctypeslib.as_array((ctypes.c_uint32 * (self.nbytes // 4)).from_address(self.ptr))
+
+    def bsk(self) -> np.ndarray:
+        return self.words()[2:2 + 500 * 6 * 2 * 1024].reshape(500, 6, 2, 1024)
+
+    def ksk(self) -> np.ndarray:
+        off = 2 + 500 * 6 * 2 * 1024
+        return self.words()[off:].reshape(1024, 8, 4, 501)
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _L is not None:
+            _L.ce_free(self.ptr)
+            self.ptr = None
+
+
+def ce_secret_keygen(seed: int) -> SecretKey:
+    p, n = ctypes.c_void_p(), ctypes.c_size_t()
+    _check(lib().ce_secret_keygen(seed, ctypes.byref(p), ctypes.byref(n)), "ce_secret_keygen")
+    return SecretKey(p.value, n.value)
+
+
+def ce_cloud_keygen(secret: SecretKey, seed: int) -> CloudKey:
+    p, n = ctypes.c_void_p(), ctypes.c_size_t()
+    _check(lib().ce_cloud_keygen(secret.ptr, seed, ctypes.byref(p), ctypes.byref(n)),
+           "ce_cloud_keygen")
+    return CloudKey(p.value, n.value)
+
+
+def ce_encrypt_bit(secret: SecretKey, bit: int, seed: int, ctr: int) -> np.ndarray:
+    out = np.zeros(LWE_WORDS, np.uint32)
+    _check(lib().ce_encrypt_bit(secret.ptr, int(bit), seed, ctr, out.ctypes.data),
+           "ce_encrypt_bit")
+    return out
+
+
+def ce_decrypt_bit(secret: SecretKey, c) -> int:
+    c = _host(c)
+    r = lib().ce_decrypt_bit(secret.ptr, c.ctypes.data)
+    if r < 0:
+        _check(r, "ce_decrypt_bit")
+    return r
+
+
+# ------------------------------------------------------------ context ---
+class Context:
+    def __init__(self, ptr: int):
+        self.ptr = ptr
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "ptr", None) and _L is not None:
+            _L.ce_destroy(self.ptr)
+        self.ptr = None
+
+
+def ce_create(device: int = 0, hbm_budget_bytes: int = 0, stream=None) -> Context:
+    p = ctypes.c_void_p()
+    _check(lib().ce_create(ctypes.byref(p), device, hbm_budget_bytes, _stream(stream)),
+           "ce_create")
+    return Context(p.value)
+
+
+def ce_destroy(ctx: Context):
+    ctx.close()
+
+
+def ce_last_error() -> str:
+    return (lib().ce_last_error() or b"").decode()
+
+
+def ce_client_admit(ctx: Context, cloud: CloudKey) -> int:
+    cid = ctypes.c_int()
+    _check(lib().ce_client_admit(ctx.ptr, cloud.ptr, cloud.nbytes, ctypes.byref(cid)),
+           "ce_client_admit")
+    return cid.value
+
+
+def ce_client_evict(ctx: Context, client: int):
+    _check(lib().ce_client_evict(ctx.ptr, client), "ce_client_evict")
+
+
+def ce_client_footprint_bytes() -> int:
+    return int(lib().ce_client_footprint_bytes())
+
+
+def _op(op) -> int:
+    return GATE_ID[op] if isinstance(op, str) else int(op)
+
+
+def ce_gate(ctx: Context, client: int, op, a, b) -> np.ndarray:
+    a, b = _host(a), _host(b)
+    out = np.zeros(LWE_WORDS, np.uint32)
+    _check(lib().ce_gate(ctx.ptr, client, _op(op), a.ctypes.data, b.ctypes.data, out.ctypes.data),
+           "ce_gate")
+    return out
+
+
+def ce_gates_batch(ctx: Context, client: int, ops, a, b, out=None) -> np.ndarray:
+    ops = _host([_op(o) for o in ops] if not isinstance(ops, np.ndarray) else ops, np.uint8)
+    a = _host(a).reshape(-1, LWE_WORDS)
+    b = _host(b).reshape(-1, LWE_WORDS)
+    n = len(ops)
+    if out is None:
+        out = np.empty((n, LWE_WORDS), np.uint32)
+    _check(lib().ce_gates_batch(ctx.ptr, client, ops.ctypes.data, a.ctypes.data, b.ctypes.data,
+                                out.ctypes.data, n), "ce_gates_batch")
+    return out
+
+
+def ce_gates_batch_device(ctx: Context, client: int, d_ops, d_a, d_b, d_out, n: int,
+                          stream=None):
+    _check(lib().ce_gates_batch_device(ctx.ptr, client, _addr(d_ops), _addr(d_a), _addr(d_b),
+                                       _addr(d_out), n, _stream(stream)), "ce_gates_batch_device")
+
+
+def ce_mux_batch_device(ctx: Context, client: int, d_a, d_b, d_c, d_out, n: int, stream=None):
+    _check(lib().ce_mux_batch_device(ctx.ptr, client, _addr(d_a), _addr(d_b), _addr(d_c),
+                                     _addr(d_out), n, _stream(stream)), "ce_mux_batch_device")
+
+
+def ce_negacyclic_mul_device(ctx: Context, d_d, d_k, d_out, n: int, stream=None):
+    _check(lib().ce_negacyclic_mul_device(ctx.ptr, _addr(d_d), _addr(d_k), _addr(d_out), n,
+                                          _stream(stream)), "ce_negacyclic_mul_device")
+
+
+def ce_set_blind_rotate_config(ctx: Context, gates_per_block: int, blocks_per_sm: int = 0):
+    _check(lib().ce_set_blind_rotate_config(ctx.ptr, gates_per_block, blocks_per_sm),
+           "ce_set_blind_rotate_config")
+
+
+def ce_last_launch_count(ctx: Context) -> int:
+    return int(lib().ce_last_launch_count(ctx.ptr))
+
+
+def ce_synchronize(ctx: Context):
+    _check(lib().ce_synchronize(ctx.ptr), "ce_synchronize")

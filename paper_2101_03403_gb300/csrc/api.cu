@@ -1,0 +1,444 @@
+// C ABI of the library: contexts, client admission, batched gates.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ce_internal.h"
+#include "launch.h"
+
+namespace ce {
+
+namespace {
+thread_local std::string g_last_error;
+
+using u128 = unsigned __int128;
+constexpr uint64_t kP = 0xFFFFFFFF00000001ull;
+
+uint64_t mulmod(uint64_t a, uint64_t b) { return uint64_t((u128(a) * b) % kP); }
+uint64_t powmod(uint64_t a, uint64_t e) {
+  uint64_t r = 1;
+  while (e) {
+    if (e & 1) r = mulmod(r, a);
+    a = mulmod(a, a);
+    e >>= 1;
+  }
+  return r;
+}
+}  // namespace
+
+ce_status set_error(ce_status code, const std::string &msg) {
+  g_last_error = msg;
+  return code;
+}
+
+// psi: a primitive 2048-th root of unity of F_p with psi^32 = 8 (so that the
+// 64-, 32- and 8-point sub-transforms use powers of two).  Found from a
+// quadratic non-residue h: h^((p-1)/2048) has order exactly 2048, and among
+// its odd powers the first with 32nd power 8 is taken.
+void transform_tables(uint64_t *out) {
+  uint64_t h = 2;
+  while (powmod(h, (kP - 1) / 2) == 1) ++h;
+  const uint64_t g = powmod(h, (kP - 1) / 2048);
+  uint64_t psi = 0;
+  for (uint64_t j = 1; j < 2048; j += 2) {
+    const uint64_t c = powmod(g, j);
+    if (powmod(c, 32) == 8) {
+      psi = c;
+      break;
+    }
+  }
+  const uint64_t psi_inv = powmod(psi, kP - 2);
+  const uint64_t inv1024 = powmod(1024, kP - 2);
+  for (int k2 = 0; k2 < 16; ++k2)
+    for (int n1 = 0; n1 < 64; ++n1) {
+      const uint64_t e = uint64_t(2 * k2 + 1) * n1;
+      out[k2 * 64 + n1] = powmod(psi, e);
+      out[1024 + k2 * 64 + n1] = mulmod(powmod(psi_inv, e), inv1024);
+    }
+}
+
+}  // namespace ce
+
+using namespace ce;
+
+namespace {
+
+constexpr uint64_t kBskNttBytes = kBskNttWords * 8;
+constexpr uint64_t kKskDevBytes = kKskDevWords * 4;
+constexpr uint64_t kClientBytes = kBskNttBytes + kKskDevBytes;
+
+struct Client {
+  bool live = false;
+  uint64_t *bsk = nullptr;  // transform-domain bootstrapping key
+  uint32_t *ksk = nullptr;  // [j][q][v-1][512]
+};
+
+ce_status cuda_fail(cudaError_t e, const char *where) {
+  return set_error(CE_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace
+
+struct ce_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sms = 0;
+  uint64_t budget = 0, used = 0;
+  std::vector<Client> clients;
+  uint64_t *tw = nullptr;
+  int *err = nullptr;
+  uint16_t *abar = nullptr;
+  uint32_t *acc = nullptr;
+  size_t job_cap = 0;
+  uint8_t *io_ops = nullptr;
+  uint32_t *io_a = nullptr, *io_b = nullptr, *io_out = nullptr;
+  size_t io_cap = 0;
+  int cfg_g = 0, cfg_bps = 0;
+  int last_launches = 0;
+};
+
+namespace {
+
+ce_status ensure_jobs(ce_ctx *ctx, size_t jobs) {
+  if (jobs <= ctx->job_cap) return CE_OK;
+  size_t cap = ctx->job_cap ? ctx->job_cap : 64;
+  while (cap < jobs) cap *= 2;
+  cudaFree(ctx->abar);
+  cudaFree(ctx->acc);
+  ctx->abar = nullptr;
+  ctx->acc = nullptr;
+  ctx->job_cap = 0;
+  cudaError_t e = cudaMalloc(&ctx->abar, cap * kAbarStride * sizeof(uint16_t));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->acc, cap * 2 * kRingN * sizeof(uint32_t));
+  if (e != cudaSuccess) return set_error(CE_ENOMEM, "scratch allocation failed");
+  ctx->job_cap = cap;
+  return CE_OK;
+}
+
+ce_status ensure_io(ce_ctx *ctx, size_t n) {
+  if (n <= ctx->io_cap) return CE_OK;
+  size_t cap = ctx->io_cap ? ctx->io_cap : 64;
+  while (cap < n) cap *= 2;
+  cudaFree(ctx->io_ops);
+  cudaFree(ctx->io_a);
+  cudaFree(ctx->io_b);
+  cudaFree(ctx->io_out);
+  ctx->io_ops = nullptr;
+  ctx->io_a = ctx->io_b = ctx->io_out = nullptr;
+  ctx->io_cap = 0;
+  const size_t w = cap * kLweWords * sizeof(uint32_t);
+  cudaError_t e = cudaMalloc(&ctx->io_ops, cap);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->io_a, w);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->io_b, w);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->io_out, w);
+  if (e != cudaSuccess) return set_error(CE_ENOMEM, "staging allocation failed");
+  ctx->io_cap = cap;
+  return CE_OK;
+}
+
+Client *find_client(ce_ctx *ctx, int id) {
+  if (id < 0 || id >= int(ctx->clients.size()) || !ctx->clients[id].live) return nullptr;
+  return &ctx->clients[id];
+}
+
+// Blind-rotation launch shape: gates per block and resident blocks per SM.
+void br_config(const ce_ctx *ctx, size_t jobs, int *G, int *blocks) {
+  int g = ctx->cfg_g, bps = ctx->cfg_bps;
+  if (g == 0) {
+    if (jobs >= size_t(8) * ctx->sms) g = 4;
+    else if (jobs >= size_t(2) * ctx->sms) g = 2;
+    else g = 1;
+  }
+  if (bps == 0) bps = (g == 1) ? 2 : 1;
+  const size_t groups = (jobs + g - 1) / g;
+  size_t b = size_t(ctx->sms) * bps;
+  if (groups < b) b = groups;
+  *G = g;
+  *blocks = int(b);
+}
+
+void ks_config(const ce_ctx *ctx, size_t n_out, int *tile, int *jsplit) {
+  int t = n_out >= 64 ? 16 : (n_out >= 4 ? 4 : 1);
+  const size_t tiles = (n_out + t - 1) / t;
+  size_t js = (size_t(2) * ctx->sms + tiles - 1) / tiles;
+  if (js < 1) js = 1;
+  if (js > 64) js = 64;
+  *tile = t;
+  *jsplit = int(js);
+}
+
+// Jobs -> blind rotation -> extraction/key switching on device buffers.
+ce_status run_path(ce_ctx *ctx, Client *cl, int mode, const uint8_t *ops, const uint32_t *a,
+                   const uint32_t *b, const uint32_t *c, uint32_t *out, size_t n,
+                   cudaStream_t st) {
+  const size_t jobs = mode ? 2 * n : n;
+  if (n == 0) {
+    ctx->last_launches = 0;
+    return CE_OK;
+  }
+  if (jobs > size_t(1) << 30) return set_error(CE_EINVAL, "batch too large");
+  ce_status s = ensure_jobs(ctx, jobs);
+  if (s != CE_OK) return s;
+  int launches = 0;
+  cudaError_t e = launch_lincomb_modswitch(ops, a, b, c, ctx->abar, int(jobs), mode, ctx->err, st);
+  if (e != cudaSuccess) return cuda_fail(e, "lincomb_modswitch");
+  ++launches;
+  int G, blocks;
+  br_config(ctx, jobs, &G, &blocks);
+  e = launch_blind_rotate(cl->bsk, ctx->abar, ctx->acc, int(jobs), ctx->tw, ctx->err, G, blocks,
+                          st);
+  if (e != cudaSuccess) return cuda_fail(e, "blind_rotate");
+  ++launches;
+  int tile, jsplit;
+  ks_config(ctx, n, &tile, &jsplit);
+  if (jsplit > 1) {
+    e = cudaMemsetAsync(out, 0, n * kLweWords * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+  }
+  e = launch_extract_keyswitch(ctx->acc, cl->ksk, out, int(n), mode != 0, tile, jsplit, st);
+  if (e != cudaSuccess) return cuda_fail(e, "extract_keyswitch");
+  ++launches;
+  ctx->last_launches = launches;
+  return CE_OK;
+}
+
+ce_status check_device_error(ce_ctx *ctx) {
+  int h = 0;
+  cudaError_t e = cudaMemcpy(&h, ctx->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "error flag read");
+  if (h) {
+    cudaMemset(ctx->err, 0, sizeof(int));
+    if (h == 2) return set_error(CE_EINVAL, "a device gate opcode was out of range");
+    return set_error(CE_ETIMEOUT, "a device-side wait expired (results invalid)");
+  }
+  return CE_OK;
+}
+
+}  // namespace
+
+extern "C" const char *ce_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" uint64_t ce_client_footprint_bytes(void) { return kClientBytes; }
+
+extern "C" ce_status ce_create(ce_ctx **out, int device, uint64_t hbm_budget_bytes,
+                               void *cuda_stream) {
+  if (!out) return set_error(CE_EINVAL, "ce_create: null output");
+  *out = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || count == 0) return set_error(CE_ECUDA, "ce_create: no CUDA device");
+  if (device < 0 || device >= count) return set_error(CE_EINVAL, "ce_create: bad device index");
+  e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  ce_ctx *ctx = new ce_ctx();
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : uint64_t(free_b) / 10 * 9;
+  std::vector<uint64_t> tw(2048);
+  transform_tables(tw.data());
+  e = cudaMalloc(&ctx->tw, 2048 * sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->err, sizeof(int));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(ctx->tw, tw.data(), 2048 * sizeof(uint64_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(ctx->err, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    ce_destroy(ctx);
+    return cuda_fail(e, "ce_create");
+  }
+  *out = ctx;
+  return CE_OK;
+}
+
+extern "C" void ce_destroy(ce_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  for (auto &c : ctx->clients) {
+    cudaFree(c.bsk);
+    cudaFree(c.ksk);
+  }
+  cudaFree(ctx->tw);
+  cudaFree(ctx->err);
+  cudaFree(ctx->abar);
+  cudaFree(ctx->acc);
+  cudaFree(ctx->io_ops);
+  cudaFree(ctx->io_a);
+  cudaFree(ctx->io_b);
+  cudaFree(ctx->io_out);
+  delete ctx;
+}
+
+extern "C" ce_status ce_client_admit(ce_ctx *ctx, const void *cloud_key, size_t bytes,
+                                     int *client_id) {
+  if (!ctx || !cloud_key || !client_id) return set_error(CE_EINVAL, "ce_client_admit: null arg");
+  const uint32_t *w = static_cast<const uint32_t *>(cloud_key);
+  if (bytes != CE_CLOUD_BYTES || w[0] != 0x4B434543u || w[1] != 1u)
+    return set_error(CE_EINVAL, "ce_client_admit: not a cloud key");
+  if (ctx->used + kClientBytes > ctx->budget)
+    return set_error(CE_EADMIT, "ce_client_admit: over the HBM budget");
+  cudaSetDevice(ctx->device);
+  Client cl;
+  uint32_t *coef = nullptr;
+  cudaError_t e = cudaMalloc(&cl.bsk, kBskNttBytes);
+  if (e == cudaSuccess) e = cudaMalloc(&cl.ksk, kKskDevBytes);
+  if (e == cudaSuccess) e = cudaMalloc(&coef, size_t(CE_BSK_WORDS) * 4);
+  if (e != cudaSuccess) {
+    cudaFree(cl.bsk);
+    cudaFree(cl.ksk);
+    cudaFree(coef);
+    return set_error(CE_ENOMEM, "ce_client_admit: device allocation failed");
+  }
+  const uint32_t *bsk = w + 2;
+  const uint32_t *ksk = bsk + CE_BSK_WORDS;
+  // Key-switching key rows v = 1..3, padded to 512 words.
+  std::vector<uint32_t> kd(kKskDevWords, 0u);
+  for (int j = 0; j < kRingN; ++j)
+    for (int q = 0; q < kKsT; ++q)
+      for (int v = 1; v < kKsBase; ++v) {
+        const uint32_t *src = ksk + ((size_t(j) * kKsT + q) * kKsBase + v) * kLweWords;
+        uint32_t *dst = kd.data() + ((size_t(j) * kKsT + q) * 3 + (v - 1)) * kKskRow;
+        std::memcpy(dst, src, kLweWords * sizeof(uint32_t));
+      }
+  cudaStream_t st = ctx->stream;
+  e = cudaMemcpyAsync(coef, bsk, size_t(CE_BSK_WORDS) * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(cl.ksk, kd.data(), kKskDevBytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_bsk_to_transform(coef, cl.bsk, ctx->tw, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(coef);
+  if (e != cudaSuccess) {
+    cudaFree(cl.bsk);
+    cudaFree(cl.ksk);
+    return cuda_fail(e, "ce_client_admit");
+  }
+  cl.live = true;
+  int id = -1;
+  for (size_t i = 0; i < ctx->clients.size(); ++i)
+    if (!ctx->clients[i].live) {
+      id = int(i);
+      break;
+    }
+  if (id < 0) {
+    id = int(ctx->clients.size());
+    ctx->clients.push_back(cl);
+  } else {
+    ctx->clients[id] = cl;
+  }
+  ctx->used += kClientBytes;
+  *client_id = id;
+  return CE_OK;
+}
+
+extern "C" ce_status ce_client_evict(ce_ctx *ctx, int client_id) {
+  if (!ctx) return set_error(CE_EINVAL, "ce_client_evict: null context");
+  Client *cl = find_client(ctx, client_id);
+  if (!cl) return set_error(CE_ENOTFOUND, "ce_client_evict: unknown client");
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  cudaFree(cl->bsk);
+  cudaFree(cl->ksk);
+  *cl = Client();
+  ctx->used -= kClientBytes;
+  return CE_OK;
+}
+
+extern "C" ce_status ce_gates_batch_device(ce_ctx *ctx, int client, const uint8_t *d_ops,
+                                           const uint32_t *d_a, const uint32_t *d_b,
+                                           uint32_t *d_out, size_t n, void *cuda_stream) {
+  if (!ctx) return set_error(CE_EINVAL, "ce_gates_batch_device: null context");
+  if (n && (!d_ops || !d_a || !d_b || !d_out))
+    return set_error(CE_EINVAL, "ce_gates_batch_device: null buffer");
+  Client *cl = find_client(ctx, client);
+  if (!cl) return set_error(CE_ENOTFOUND, "ce_gates_batch_device: unknown client");
+  cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
+  return run_path(ctx, cl, 0, d_ops, d_a, d_b, nullptr, d_out, n, st);
+}
+
+extern "C" ce_status ce_mux_batch_device(ce_ctx *ctx, int client, const uint32_t *d_a,
+                                         const uint32_t *d_b, const uint32_t *d_c,
+                                         uint32_t *d_out, size_t n, void *cuda_stream) {
+  if (!ctx) return set_error(CE_EINVAL, "ce_mux_batch_device: null context");
+  if (n && (!d_a || !d_b || !d_c || !d_out))
+    return set_error(CE_EINVAL, "ce_mux_batch_device: null buffer");
+  Client *cl = find_client(ctx, client);
+  if (!cl) return set_error(CE_ENOTFOUND, "ce_mux_batch_device: unknown client");
+  cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
+  return run_path(ctx, cl, 1, nullptr, d_a, d_b, d_c, d_out, n, st);
+}
+
+extern "C" ce_status ce_gates_batch(ce_ctx *ctx, int client, const uint8_t *ops,
+                                    const ce_lwe *a, const ce_lwe *b, ce_lwe *out, size_t n) {
+  if (!ctx) return set_error(CE_EINVAL, "ce_gates_batch: null context");
+  if (n == 0) return CE_OK;
+  if (!ops || !a || !b || !out) return set_error(CE_EINVAL, "ce_gates_batch: null buffer");
+  for (size_t i = 0; i < n; ++i)
+    if (ops[i] > CE_ORYN) return set_error(CE_EINVAL, "ce_gates_batch: bad gate opcode");
+  Client *cl = find_client(ctx, client);
+  if (!cl) return set_error(CE_ENOTFOUND, "ce_gates_batch: unknown client");
+  cudaSetDevice(ctx->device);
+  ce_status s = ensure_io(ctx, n);
+  if (s != CE_OK) return s;
+  cudaStream_t st = ctx->stream;
+  const size_t w = n * kLweWords * sizeof(uint32_t);
+  cudaError_t e = cudaMemcpyAsync(ctx->io_ops, ops, n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->io_a, a, w, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->io_b, b, w, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "ce_gates_batch upload");
+  s = run_path(ctx, cl, 0, ctx->io_ops, ctx->io_a, ctx->io_b, nullptr, ctx->io_out, n, st);
+  if (s != CE_OK) return s;
+  e = cudaMemcpyAsync(out, ctx->io_out, w, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "ce_gates_batch");
+  return check_device_error(ctx);
+}
+
+extern "C" ce_status ce_gate(ce_ctx *ctx, int client, ce_gate_op op, const ce_lwe *a,
+                             const ce_lwe *b, ce_lwe *out) {
+  const uint8_t o = static_cast<uint8_t>(op);
+  if (int(op) < 0 || int(op) > CE_ORYN) return set_error(CE_EINVAL, "ce_gate: bad opcode");
+  return ce_gates_batch(ctx, client, &o, a, b, out, 1);
+}
+
+extern "C" ce_status ce_negacyclic_mul_device(ce_ctx *ctx, const int16_t *d_d,
+                                              const uint32_t *d_k, uint32_t *d_out, size_t n,
+                                              void *cuda_stream) {
+  if (!ctx) return set_error(CE_EINVAL, "ce_negacyclic_mul_device: null context");
+  if (n && (!d_d || !d_k || !d_out))
+    return set_error(CE_EINVAL, "ce_negacyclic_mul_device: null buffer");
+  if (n > (size_t(1) << 28)) return set_error(CE_EINVAL, "ce_negacyclic_mul_device: n too large");
+  cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
+  cudaError_t e = launch_negacyclic_mul(d_d, d_k, d_out, int(n), ctx->tw, st);
+  if (e != cudaSuccess) return cuda_fail(e, "negacyclic_mul");
+  return CE_OK;
+}
+
+extern "C" ce_status ce_set_blind_rotate_config(ce_ctx *ctx, int gates_per_block,
+                                                int blocks_per_sm) {
+  if (!ctx) return set_error(CE_EINVAL, "ce_set_blind_rotate_config: null context");
+  if (!(gates_per_block == 0 || gates_per_block == 1 || gates_per_block == 2 ||
+        gates_per_block == 4))
+    return set_error(CE_EINVAL, "gates_per_block must be 0, 1, 2 or 4");
+  const int max_bps = gates_per_block == 1 ? 2 : 1;
+  if (blocks_per_sm < 0 || (gates_per_block && blocks_per_sm > max_bps))
+    return set_error(CE_EINVAL, "blocks_per_sm exceeds what shared memory allows");
+  ctx->cfg_g = gates_per_block;
+  ctx->cfg_bps = blocks_per_sm;
+  return CE_OK;
+}
+
+extern "C" int ce_last_launch_count(ce_ctx *ctx) { return ctx ? ctx->last_launches : 0; }
+
+extern "C" ce_status ce_synchronize(ce_ctx *ctx) {
+  if (!ctx) return set_error(CE_EINVAL, "ce_synchronize: null context");
+  cudaError_t e = ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(e, "ce_synchronize");
+  return check_device_error(ctx);
+}

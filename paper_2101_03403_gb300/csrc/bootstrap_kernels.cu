@@ -1,0 +1,486 @@
+// GPU kernels of the gate-bootstrapping path (sm_103a):
+//   lincomb_modswitch  — gate linear combination + modulus switch to 2N
+//   blind_rotate       — persistent batched blind rotation (n CMux steps)
+//   extract_keyswitch  — fused sample extraction + LWE key switching
+//   bsk_to_transform   — bootstrapping key to the transform domain (admission)
+//   negacyclic_mul     — exact digit x key products (verification entry point)
+// The bootstrapping construction is the TFHE one the paper builds its gates
+// on (§3 "TFHE Library": one bootstrap per binary gate, two for MUX).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ce_internal.h"
+#include "gl_field.cuh"
+#include "launch.h"
+#include "ntt_pair.cuh"
+
+namespace ce {
+
+namespace {
+
+// Gate linear parts (0, kappa/8) + s1 c1 + s2 c2 (truth tables: §3, Table
+// "TFHE API Benchmark"; constants give each row the largest margin from the
+// decision boundaries for +-1/8 inputs).  Index 10 = the first MUX half
+// (AND of a, b), 11 = the second (ANDNY of a, c).
+__constant__ int8_t c_kappa8[12] = {1, -1, 1, 2, -1, -2, -1, -1, 1, 1, -1, -1};
+__constant__ int8_t c_s1[12] = {-1, 1, 1, 2, -1, -2, -1, 1, -1, 1, 1, -1};
+__constant__ int8_t c_s2[12] = {-1, 1, 1, 2, -1, -2, 1, -1, 1, -1, 1, 1};
+
+// Gadget decomposition offset: rounding to 30 bits (+2^1) plus Bg/2 at each
+// of the three digit positions (2^31 + 2^21 + 2^11).  Digit p (1..3) of x is
+// ((x + offset) >> (32 - 10 p) & 1023) - 512.
+constexpr uint32_t kDecompOffset = 0x80200802u;
+
+// ------------------------------------------------------------------- K1 ---
+// One block per job: the gate's linear combination of its two inputs and the
+// modulus switch of every word, abar = round(x * 2048 / 2^32) mod 2048.
+// mode 0: job g = gate ops[g](a[g], b[g]).  mode 1: MUX, job 2i = AND-part of
+// (a[i], b[i]), job 2i+1 = ANDNY-part of (a[i], c[i]).
+__global__ void __launch_bounds__(512) lincomb_modswitch_kernel(
+    const uint8_t *__restrict__ ops, const uint32_t *__restrict__ a,
+    const uint32_t *__restrict__ b, const uint32_t *__restrict__ c,
+    uint16_t *__restrict__ abar, int mode, int *__restrict__ err) {
+  const int job = blockIdx.x;
+  int op, src1, src2;
+  const uint32_t *second = b;
+  if (mode == 0) {
+    op = ops[job];
+    if (op > 9) {  // not a gate opcode: flag it and evaluate NAND instead
+      if (threadIdx.x == 0) atomicExch(err, 2);
+      op = 0;
+    }
+    src1 = src2 = job;
+  } else {
+    op = 10 + (job & 1);
+    src1 = src2 = job >> 1;
+    if (job & 1) second = c;
+  }
+  const int m = threadIdx.x;
+  if (m < kLweWords) {
+    const uint32_t x = uint32_t(int32_t(c_s1[op])) * a[size_t(src1) * kLweWords + m] +
+                       uint32_t(int32_t(c_s2[op])) * second[size_t(src2) * kLweWords + m] +
+                       (m == kLweN ? uint32_t(int32_t(c_kappa8[op])) * kMuEighth : 0u);
+    abar[size_t(job) * kAbarStride + m] = uint16_t(((x + (1u << 20)) >> 21) & 2047u);
+  }
+}
+
+// ------------------------------------------------------------------- K2 ---
+// Persistent batched blind rotation.  A block holds G gates (128 threads
+// each) and streams the bootstrapping key once per block: the transform-
+// domain rows of CMux step i, gadget level p (4 polynomials, 32 KB) arrive by
+// bulk asynchronous copy into a ring of NSLOT shared-memory slots and are
+// used by all G gates.  The last warp to finish with a slot refills it.
+//
+// Per gate and step i (a CMux controlled by key bit s_i): D = X^abar_i ACC -
+// ACC; for p = 1..3: forward-transform digit p of both halves of D, multiply
+// by the key rows and accumulate in the transform domain; then one inverse
+// transform of the two accumulators and ACC += result (exact mod 2^32).
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_timer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
+
+// Bounded wait for a slot's copy; on expiry the block records the error,
+// raises its abort flag and continues without waiting (results are then
+// invalid and the host reports CE_ETIMEOUT).
+__device__ __forceinline__ void wait_slot(uint32_t bar, uint32_t parity, volatile int *abort,
+                                          int *err) {
+  if (mbar_try_wait(bar, parity)) return;
+  const uint64_t t0 = global_timer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort) return;
+    if (global_timer() - t0 > kWaitLimitNs) {
+      *abort = 1;
+      atomicExch(err, 1);
+      return;
+    }
+  }
+}
+
+__device__ __forceinline__ void issue_chunk(uint64_t *slot, uint32_t bar, const uint64_t *src) {
+  constexpr uint32_t kBytes = kChunkWords * 8;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kBytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(slot)),
+      "l"(src), "r"(kBytes), "r"(bar)
+      : "memory");
+}
+
+template <int G, int NSLOT>
+struct BrSmem {
+  static constexpr size_t kRing = size_t(NSLOT) * kChunkWords * 8;
+  static constexpr size_t kAcc = 2 * kRingN * 4;                 // per gate
+  static constexpr size_t kBuf = size_t(ntt::kBufWords) * 8;     // per gate
+  static constexpr size_t kGate = kAcc + kBuf;
+  static constexpr size_t kBars = 64;
+  static constexpr size_t kTotal = kRing + G * kGate + kBars + 64;
+};
+
+template <int G, int NSLOT>
+__global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
+    const uint64_t *__restrict__ bsk, const uint16_t *__restrict__ abar,
+    uint32_t *__restrict__ acc_out, int n_jobs, const uint64_t *__restrict__ tw,
+    int *__restrict__ err) {
+  using L = BrSmem<G, NSLOT>;
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint64_t *ring = reinterpret_cast<uint64_t *>(smem);
+  const int g = threadIdx.x >> 7, t = threadIdx.x & 127, lane = threadIdx.x & 31;
+  uint32_t *acc = reinterpret_cast<uint32_t *>(smem + L::kRing + g * L::kGate);
+  uint64_t *buf = reinterpret_cast<uint64_t *>(smem + L::kRing + g * L::kGate + L::kAcc);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::kRing + G * L::kGate);
+  uint32_t *count = reinterpret_cast<uint32_t *>(full + NSLOT);
+  volatile int *abort = reinterpret_cast<volatile int *>(count + NSLOT);
+  const int bar = 1 + g;
+  const uint64_t *tw_fwd = tw, *tw_inv = tw + 1024;
+  constexpr int kChunksPerGate = kLweN * kGadgetL;  // 1500
+  constexpr int kWarps = 4 * G;
+
+  const int n_groups = (n_jobs + G - 1) / G;
+  const int my_groups =
+      blockIdx.x < n_groups ? (n_groups - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
+  const int total_chunks = my_groups * kChunksPerGate;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSLOT; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(full + s)) : "memory");
+      count[s] = 0;
+    }
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < NSLOT && c < total_chunks; ++c)
+      issue_chunk(ring + size_t(c) * kChunkWords, smem_u32(full + c),
+                  bsk + size_t(c % kChunksPerGate) * kChunkWords);
+  }
+
+  const int P = t >> 6, n1 = t & 63;
+  int chunk = 0;
+  for (int jg = 0; jg < my_groups; ++jg) {
+    const int job = (blockIdx.x + jg * gridDim.x) * G + g;
+    const bool active = job < n_jobs;
+    const uint16_t *ab = abar + size_t(active ? job : 0) * kAbarStride;
+
+    // ACC = (0, X^(-bbar) v), v = mu * sum_j X^j, mu = +1/8.
+    {
+      const int bbar = active ? ab[kLweN] : 0;
+      const int k = (2 * kRingN - bbar) & (2 * kRingN - 1);
+      for (int j = t; j < kRingN; j += 128) {
+        acc[j] = 0;
+        const bool hi = k < kRingN ? (j >= k) : (j < k - kRingN);
+        acc[kRingN + j] = hi ? kMuEighth : 0u - kMuEighth;
+      }
+    }
+    ntt::named_bar(bar);
+
+    for (int i = 0; i < kLweN; ++i) {
+      const int rot = active ? __ldg(ab + i) : 0;
+      uint32_t w[16];
+      uint64_t X[2][8];
+      if (rot != 0) {
+        // w = X^rot ACC_P - ACC_P + decomposition offset, at n = n1 + 64 n2.
+        const uint32_t *src = acc + P * kRingN;
+        const int kk = rot & (kRingN - 1);
+        const uint32_t flip = (rot >= kRingN) ? 0xFFFFFFFFu : 0u;
+#pragma unroll
+        for (int n2 = 0; n2 < 16; ++n2) {
+          const int n = n1 + 64 * n2;
+          const int s = n - kk;
+          uint32_t r = s >= 0 ? src[s] : 0u - src[s + kRingN];
+          r = (r ^ flip) - flip;  // negate when rot >= N (X^N = -1)
+          w[n2] = r - src[n] + kDecompOffset;
+        }
+#pragma unroll
+        for (int o = 0; o < 2; ++o)
+#pragma unroll
+          for (int d = 0; d < 8; ++d) X[o][d] = 0;
+      }
+#pragma unroll 1
+      for (int pz = 0; pz < kGadgetL; ++pz, ++chunk) {
+        const int slot = chunk % NSLOT;
+        wait_slot(smem_u32(full + slot), uint32_t(chunk / NSLOT) & 1u, abort, err);
+        if (rot != 0) {
+          uint64_t v[16], Y[2][8];
+          const int sh = 22 - 10 * pz;
+#pragma unroll
+          for (int n2 = 0; n2 < 16; ++n2)
+            v[n2] = gl::from_i32(int32_t((w[n2] >> sh) & 1023u) - 512);
+          ntt::forward(v, Y, buf, t, bar, tw_fwd);
+          // X[o] += Y[0] * key(c=0, p, o) + Y[1] * key(c=1, p, o)
+          const uint64_t *key = ring + size_t(slot) * kChunkWords + t;
+#pragma unroll
+          for (int d = 0; d < 8; ++d) {
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+              const uint64_t k0 = key[((0 * 2 + o) * 8 + d) * 128];
+              const uint64_t k1 = key[((1 * 2 + o) * 8 + d) * 128];
+              X[o][d] = gl::add(X[o][d], gl::add(gl::mul(Y[0][d], k0), gl::mul(Y[1][d], k1)));
+            }
+          }
+        }
+        // Release the slot; the last warp out refills it with chunk + NSLOT.
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence_block();
+          const uint32_t old = atomicAdd(count + slot, 1u);
+          if (old == kWarps - 1) {
+            count[slot] = 0;
+            __threadfence_block();
+            const int next = chunk + NSLOT;
+            if (next < total_chunks && !*abort)
+              issue_chunk(ring + size_t(slot) * kChunkWords, smem_u32(full + slot),
+                          bsk + size_t(next % kChunksPerGate) * kChunkWords);
+          }
+        }
+      }
+      if (rot != 0) {
+        uint64_t v[16];
+        ntt::inverse(X, v, buf, t, bar, tw_inv);
+        uint32_t *dst = acc + P * kRingN + n1;
+#pragma unroll
+        for (int n2 = 0; n2 < 16; ++n2) dst[64 * n2] += gl::lift32(v[n2]);
+      }
+      ntt::named_bar(bar);
+    }
+    if (active) {
+      uint32_t *out = acc_out + size_t(job) * 2 * kRingN;
+      for (int j = t; j < 2 * kRingN; j += 128) out[j] = acc[j];
+    }
+    ntt::named_bar(bar);
+  }
+}
+
+// ------------------------------------------------------------------- K4 ---
+// Fused sample extraction (coefficient 0: a'_0 = A_0, a'_j = -A_{N-j},
+// b' = B_0) and key switching: each a'_j rounded to 16 bits, split into 8
+// base-4 digits (most significant first), out = (0, b') - sum KSK[j][q][digit].
+// A block serves GT jobs for a range of j; the three KSK rows of (j, q) are
+// read once (uint4 per thread) and applied to all GT jobs.  With several
+// j-ranges the partial sums are added atomically (exact mod 2^32).  In MUX
+// mode an output combines jobs 2i and 2i+1 plus (0, +1/8) before switching.
+template <int GT, bool MUX>
+__global__ void __launch_bounds__(128) extract_keyswitch_kernel(
+    const uint32_t *__restrict__ acc, const uint32_t *__restrict__ ksk,
+    uint32_t *__restrict__ out, int n_out, int jchunk) {
+  extern __shared__ uint16_t hbits[];  // [GT][jchunk]
+  const int tile = blockIdx.x, j0 = blockIdx.y * jchunk;
+  const int j1 = min(kRingN, j0 + jchunk);
+  for (int idx = threadIdx.x; idx < GT * jchunk; idx += 128) {
+    const int g = idx / jchunk, j = j0 + idx % jchunk;
+    const int o = tile * GT + g;
+    uint32_t h = 0;
+    if (o < n_out && j < j1) {
+      const uint32_t *A = acc + size_t(MUX ? 2 * o : o) * 2 * kRingN;
+      uint32_t aj = (j == 0) ? A[0] : 0u - A[kRingN - j];
+      if (MUX) {
+        const uint32_t *A2 = A + 2 * kRingN;
+        aj += (j == 0) ? A2[0] : 0u - A2[kRingN - j];
+      }
+      h = (aj + 0x8000u) >> 16;
+    }
+    hbits[idx] = uint16_t(h);
+  }
+  __syncthreads();
+
+  uint32_t s[GT][4];
+#pragma unroll
+  for (int g = 0; g < GT; ++g)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) s[g][e] = 0;
+  const uint4 *K = reinterpret_cast<const uint4 *>(ksk) + threadIdx.x;
+#pragma unroll 1
+  for (int j = j0; j < j1; ++j) {
+#pragma unroll 2
+    for (int q = 0; q < kKsT; ++q) {
+      const size_t row = (size_t(j) * kKsT + q) * 3;
+      const uint4 k1 = __ldg(K + (row + 0) * (kKskRow / 4));
+      const uint4 k2 = __ldg(K + (row + 1) * (kKskRow / 4));
+      const uint4 k3 = __ldg(K + (row + 2) * (kKskRow / 4));
+      const int shift = 14 - 2 * q;
+#pragma unroll
+      for (int g = 0; g < GT; ++g) {
+        const uint32_t dg = (uint32_t(hbits[g * jchunk + (j - j0)]) >> shift) & 3u;
+        const uint4 sel = dg == 1 ? k1 : (dg == 2 ? k2 : k3);
+        const uint32_t m = dg ? 0xFFFFFFFFu : 0u;
+        s[g][0] += sel.x & m;
+        s[g][1] += sel.y & m;
+        s[g][2] += sel.z & m;
+        s[g][3] += sel.w & m;
+      }
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < GT; ++g) {
+    const int o = tile * GT + g;
+    if (o >= n_out) break;
+    const uint32_t *A = acc + size_t(MUX ? 2 * o : o) * 2 * kRingN;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int m = 4 * threadIdx.x + e;
+      if (m >= kLweWords) continue;
+      uint32_t val = 0u - s[g][e];
+      if (m == kLweN && blockIdx.y == 0) {
+        uint32_t bp = A[kRingN];
+        if (MUX) bp += A[2 * kRingN + kRingN] + kMuEighth;
+        val += bp;
+      }
+      if (gridDim.y == 1)
+        out[size_t(o) * kLweWords + m] = val;
+      else
+        atomicAdd(out + size_t(o) * kLweWords + m, val);
+    }
+  }
+}
+
+// --------------------------------------------------------- key to transform ---
+// Block (i, p): transforms the four polynomials (TRGSW half c, component o)
+// of bootstrapping-key rows r = c*3 + p of key bit i and stores them in the
+// [i][p][c*2+o][d][thread] order the blind rotation reads.
+__global__ void __launch_bounds__(128) bsk_to_transform_kernel(const uint32_t *__restrict__ bsk,
+                                                               uint64_t *__restrict__ out,
+                                                               const uint64_t *__restrict__ tw) {
+  __shared__ uint64_t buf[ntt::kBufWords];
+  const int i = blockIdx.x / kGadgetL, pz = blockIdx.x % kGadgetL, t = threadIdx.x;
+  const int P = t >> 6, n1 = t & 63;
+  for (int c = 0; c < 2; ++c) {
+    const uint32_t *row = bsk + ((size_t(i) * 2 * kGadgetL + c * kGadgetL + pz) * 2 + P) * kRingN;
+    uint64_t v[16], X[2][8];
+#pragma unroll
+    for (int n2 = 0; n2 < 16; ++n2) v[n2] = row[n1 + 64 * n2];
+    ntt::forward(v, X, buf, t, 1, tw);
+    uint64_t *dst = out + size_t(blockIdx.x) * kChunkWords;
+#pragma unroll
+    for (int o = 0; o < 2; ++o)
+#pragma unroll
+      for (int d = 0; d < 8; ++d) dst[((c * 2 + o) * 8 + d) * 128 + t] = X[o][d];
+  }
+}
+
+// ---------------------------------------------------------- negacyclic mul ---
+// Block b: products 2b and 2b+1 (d signed 16-bit, k uint32), exact mod 2^32.
+__global__ void __launch_bounds__(128) negacyclic_mul_kernel(const int16_t *__restrict__ dg,
+                                                             const uint32_t *__restrict__ k,
+                                                             uint32_t *__restrict__ out, int n,
+                                                             const uint64_t *__restrict__ tw) {
+  __shared__ uint64_t buf[ntt::kBufWords];
+  const int t = threadIdx.x, P = t >> 6, n1 = t & 63;
+  const int prod = 2 * blockIdx.x + P;
+  const bool live = prod < n;
+  uint64_t v[16], XD[2][8], XK[2][8];
+#pragma unroll
+  for (int n2 = 0; n2 < 16; ++n2)
+    v[n2] = live ? gl::from_i32(dg[size_t(prod) * kRingN + n1 + 64 * n2]) : 0;
+  ntt::forward(v, XD, buf, t, 1, tw);
+#pragma unroll
+  for (int n2 = 0; n2 < 16; ++n2) v[n2] = live ? k[size_t(prod) * kRingN + n1 + 64 * n2] : 0;
+  ntt::forward(v, XK, buf, t, 1, tw);
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int d = 0; d < 8; ++d) XD[q][d] = gl::mul(XD[q][d], XK[q][d]);
+  ntt::inverse(XD, v, buf, t, 1, tw + 1024);
+  if (live) {
+#pragma unroll
+    for (int n2 = 0; n2 < 16; ++n2) out[size_t(prod) * kRingN + n1 + 64 * n2] = gl::lift32(v[n2]);
+  }
+}
+
+template <int G, int NSLOT>
+cudaError_t launch_br(const uint64_t *bsk, const uint16_t *abar, uint32_t *acc, int n,
+                      const uint64_t *tw, int *err, int blocks, cudaStream_t st) {
+  using L = BrSmem<G, NSLOT>;
+  auto kern = blind_rotate_kernel<G, NSLOT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(L::kTotal));
+  if (e != cudaSuccess) return e;
+  kern<<<blocks, 128 * G, L::kTotal, st>>>(bsk, abar, acc, n, tw, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t blind_rotate_smem_bytes(int gates_per_block) {
+  switch (gates_per_block) {
+    case 1: return BrSmem<1, 2>::kTotal;
+    case 2: return BrSmem<2, 3>::kTotal;
+    default: return BrSmem<4, 3>::kTotal;
+  }
+}
+
+cudaError_t launch_lincomb_modswitch(const uint8_t *ops, const uint32_t *a, const uint32_t *b,
+                                     const uint32_t *c, uint16_t *abar, int n_jobs, int mode,
+                                     int *err, cudaStream_t st) {
+  if (n_jobs <= 0) return cudaSuccess;
+  lincomb_modswitch_kernel<<<n_jobs, 512, 0, st>>>(ops, a, b, c, abar, mode, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_blind_rotate(const uint64_t *bsk, const uint16_t *abar, uint32_t *acc,
+                                int n_jobs, const uint64_t *tw, int *err, int gates_per_block,
+                                int blocks, cudaStream_t st) {
+  if (n_jobs <= 0) return cudaSuccess;
+  switch (gates_per_block) {
+    case 1: return launch_br<1, 2>(bsk, abar, acc, n_jobs, tw, err, blocks, st);
+    case 2: return launch_br<2, 3>(bsk, abar, acc, n_jobs, tw, err, blocks, st);
+    default: return launch_br<4, 3>(bsk, abar, acc, n_jobs, tw, err, blocks, st);
+  }
+}
+
+cudaError_t launch_extract_keyswitch(const uint32_t *acc, const uint32_t *ksk, uint32_t *out,
+                                     int n_out, bool mux, int tile, int jsplit, cudaStream_t st) {
+  if (n_out <= 0) return cudaSuccess;
+  const int jchunk = (kRingN + jsplit - 1) / jsplit;
+  const dim3 grid((n_out + tile - 1) / tile, jsplit);
+  const size_t sm = size_t(tile) * jchunk * sizeof(uint16_t);
+  if (tile == 1) {
+    if (mux) extract_keyswitch_kernel<1, true><<<grid, 128, sm, st>>>(acc, ksk, out, n_out, jchunk);
+    else extract_keyswitch_kernel<1, false><<<grid, 128, sm, st>>>(acc, ksk, out, n_out, jchunk);
+  } else if (tile == 4) {
+    if (mux) extract_keyswitch_kernel<4, true><<<grid, 128, sm, st>>>(acc, ksk, out, n_out, jchunk);
+    else extract_keyswitch_kernel<4, false><<<grid, 128, sm, st>>>(acc, ksk, out, n_out, jchunk);
+  } else {
+    if (mux) extract_keyswitch_kernel<16, true><<<grid, 128, sm, st>>>(acc, ksk, out, n_out, jchunk);
+    else extract_keyswitch_kernel<16, false><<<grid, 128, sm, st>>>(acc, ksk, out, n_out, jchunk);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bsk_to_transform(const uint32_t *bsk, uint64_t *out, const uint64_t *tw,
+                                    cudaStream_t st) {
+  bsk_to_transform_kernel<<<kLweN * kGadgetL, 128, 0, st>>>(bsk, out, tw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_negacyclic_mul(const int16_t *d, const uint32_t *k, uint32_t *out, int n,
+                                  const uint64_t *tw, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  negacyclic_mul_kernel<<<(n + 1) / 2, 128, 0, st>>>(d, k, out, n, tw);
+  return cudaGetLastError();
+}
+
+}  // namespace ce

@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 gate-bootstrapping path.
+
+Metric: bootstrapped gates per second on one GB300 (exact: every output is
+the bit-exact result of the plain definition).  A step is one pass of the
+whole hot path (linear combination + modulus switch, blind rotation, sample
+extraction + key switching) over one level of 8192 independent gates: the
+first level of the 16-bit parallel-prefix adder (one AND and one XOR per bit,
+§5 "Adder", Stage 1) for 256 encrypted operand pairs.  Inputs are synthetic
+and seeded (fresh encryptions of uniform random bits under keys generated
+from seed 20210103).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+`value` uses device-resident inputs (device-side time of K steps, L2 flushed
+between steps); `e2e` runs the same work through the host-buffer C-ABI call
+(ce_gates_batch) with the host<->device copies inside the timed region.
+`--impl reference` times the plain CPU oracle (test infrastructure, used here
+only as the reference arm) on a bounded sample of the same workload.
+Under torchrun every rank evaluates its own batch (independent gates, no
+data-path collective) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SEED = 20210103
+N_GATES = 8192
+METRIC = "bootstrapped gates/s on 1 GB300 (exact)"
+UNIT = "gates/s"
+# Algorithmic work of one bootstrap, counted as 64-bit modular multiplications
+# of the transform method: per CMux step 6 forward + 2 inverse 1024-point
+# transforms (512 * 10 butterflies each) and 12 * 1024 pointwise products.
+MODMUL_PER_CMUX = 8 * 512 * 10 + 12 * 1024          # 53,248
+MODMUL_PER_GATE = 500 * MODMUL_PER_CMUX               # 26,624,000
+# ALU peak derived from unit counts: 152 SMs x 64 INT32 lanes x 2.07 GHz,
+# at >= 16 32-bit integer operations per 64-bit Goldilocks multiply.
+INT32_OPS_PER_S = 152 * 64 * 2.07e9
+OPS_PER_MODMUL = 16
+PEAK_GMODMUL = INT32_OPS_PER_S / OPS_PER_MODMUL / 1e9
+KERNEL_SOURCES = ["bootstrap_kernels.cu", "ntt_pair.cuh", "gl_field.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--gates", type=int, default=N_GATES)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------ distributed ---
+def dist_setup(backend: str):
+    """Rank/world from the torchrun environment (single process otherwise)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(units_per_rank: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput: units all ranks processed / slowest rank's time."""
+    return units_per_rank * steps * world / (max_ms / 1e3)
+
+
+# ----------------------------------------------------------------- clocks ---
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.samples, self.stop = index, [], threading.Event()
+        self.th = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        while not self.stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([v.strip() for v in out.split(",")])
+            except Exception:
+                pass
+            self.stop.wait(0.2)
+
+    def __enter__(self):
+        self.th.start()
+        return self
+
+    def __exit__(self, *a):
+        self.stop.set()
+        self.th.join(timeout=10)
+
+    def summary(self) -> dict:
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 3 + i and s[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------ oracle ---
+def oracle_sample(n_gates: int, threads: int):
+    """Time the plain CPU oracle on n_gates gates of the same workload."""
+    from oracle import oracle as O
+    keys = O.keygen(O.GATE_PARAMS, SEED)
+    rng = np.random.default_rng(SEED)
+    bits = rng.integers(0, 2, (n_gates, 2))
+    p = O.GATE_PARAMS
+    ca = np.stack([O.encrypt(p, keys.s, int(b), 31, i) for i, b in enumerate(bits[:, 0])])
+    cb = np.stack([O.encrypt(p, keys.s, int(b), 32, i) for i, b in enumerate(bits[:, 1])])
+    ops = np.tile([1, 3], n_gates // 2 + 1)[:n_gates]
+    t0 = time.perf_counter()
+    O.gates(keys, ops, ca, cb, threads=threads)
+    return n_gates / (time.perf_counter() - t0)
+
+
+def cpu_cores() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    cores = cpu_cores()
+    per_step = cores  # one gate per core per step (~5 s of CPU work per core)
+    for _ in range(args.warmup):
+        oracle_sample(per_step, cores)
+    vals, t_all = [], 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        vals.append(oracle_sample(per_step, cores))
+        t_all += time.perf_counter() - t0
+    value = per_step * args.steps / t_all
+    sample = f"{per_step} gates (AND/XOR) of the {args.gates}-gate level per step, one gate per core"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_all / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (seeded encryptions of uniform bits)",
+            "config": {"workload": f"adder level 1: {args.gates} bootstrapped AND/XOR gates "
+                                   "(256 x 16-bit operand pairs), n=500 N=1024 l=3 Bg=2^10 t=8",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- our arm ---
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2101_03403_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(kernel)
+    except Exception:
+        return None
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def run_ours(args, rank: int, world: int, local: int):
+    import torch
+
+    import paper_2101_03403_gb300 as ce
+    from paper_2101_03403_gb300 import build as b
+    b.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.gates
+    sk = ce.ce_secret_keygen(SEED)
+    ck = ce.ce_cloud_keygen(sk, SEED)
+    stream = torch.cuda.current_stream(dev)
+    ctx = ce.ce_create(local, 0, stream)
+    cid = ce.ce_client_admit(ctx, ck)
+
+    rng = np.random.default_rng(SEED + rank)
+    bits = rng.integers(0, 2, (n, 2))
+    ca = np.stack([ce.ce_encrypt_bit(sk, int(v), 31 + 2 * rank, i) for i, v in enumerate(bits[:, 0])])
+    cb = np.stack([ce.ce_encrypt_bit(sk, int(v), 32 + 2 * rank, i) for i, v in enumerate(bits[:, 1])])
+    ops = np.tile(np.array([1, 3], np.uint8), n // 2 + 1)[:n]        # AND, XOR per bit
+    d_ops = torch.from_numpy(ops).to(dev)
+    d_a = torch.from_numpy(ca.view(np.int32)).to(dev)
+    d_b = torch.from_numpy(cb.view(np.int32)).to(dev)
+    d_out = torch.empty((n, 501), dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # > 129 MB L2
+
+    def step():
+        ce.ce_gates_batch_device(ctx, cid, d_ops, d_a, d_b, d_out, n, stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    ce.ce_synchronize(ctx)
+
+    # correctness guard on the measured output: decrypt a sample
+    out = d_out.cpu().numpy().view(np.uint32)
+    truth = np.where(ops == 1, bits[:, 0] & bits[:, 1], bits[:, 0] ^ bits[:, 1])
+    for i in rng.choice(n, 64, replace=False):
+        assert ce.ce_decrypt_bit(sk, out[i]) == truth[i], "wrong gate output"
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ce.ce_profile_enable(ctx, True)
+    launches0 = 0
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        for k in range(args.steps):
+            flush.zero_()                      # outside the per-step events
+            starts[k].record(stream)
+            step()
+            launches0 += ce.ce_last_launch_count(ctx)
+            ends[k].record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+    ce.ce_synchronize(ctx)
+    prof = ce.ce_profile_read(ctx)
+    ce.ce_profile_enable(ctx, False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    value = weak_scaling_value(n, args.steps, world, total_ms)
+
+    # end to end through the host-buffer call, copies included
+    pin_ops = torch.from_numpy(ops).pin_memory()
+    pin_a = torch.from_numpy(ca).pin_memory()
+    pin_b = torch.from_numpy(cb).pin_memory()
+    pin_out = torch.empty((n, 501), dtype=torch.int32).pin_memory()
+    lib = ce.lib()
+
+    def e2e_step():
+        r = lib.ce_gates_batch(ctx.ptr, cid, pin_ops.data_ptr(), pin_a.data_ptr(), pin_b.data_ptr(),
+                               pin_out.data_ptr(), n)
+        if r != 0:
+            raise RuntimeError(ce.ce_last_error())
+
+    e2e_step()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e_val = n * args.steps * world / e2e_s
+    assert (pin_out.numpy().view(np.uint32) == out).all(), "e2e output differs"
+
+    br_ms, br_launches = prof["blind_rotate"]
+    br_avg = br_ms / max(br_launches, 1)
+    achieved = n * MODMUL_PER_GATE / (br_avg / 1e3) / 1e9
+    roof = {"kernel": "blind_rotate", "bound": "alu", "achieved": achieved,
+            "peak": PEAK_GMODMUL, "unit": "Gmodmul/s", "frac": achieved / PEAK_GMODMUL,
+            "traffic": recorded_traffic("blind_rotate"),
+            "peak_note": "derived: 152 SMs x 64 INT32 lanes x 2.07 GHz / 16 ops per modmul",
+            "kernel_ms": {k: v[0] / max(v[1], 1) for k, v in prof.items()}}
+
+    cpu = None
+    if rank == 0 and world == 1:
+        cores = cpu_cores()
+        g = 2 * cores
+        cpu = {"value": oracle_sample(g, cores), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{g} gates (AND/XOR) of the {n}-gate level, one gate per thread"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+                "data": "synthetic (seeded encryptions of uniform bits)",
+                "config": {"workload": f"adder level 1: {n} bootstrapped AND/XOR gates "
+                                       "(256 x 16-bit operand pairs), n=500 N=1024 l=3 "
+                                       "Bg=2^10 t=8", "gates_per_step_per_gpu": n,
+                           "l2": "flushed between steps (256 MB write)",
+                           "parallelism": f"independent batches x{world}"},
+                "e2e": {"value": e2e_val, "unit": UNIT,
+                        "h2d_bytes_per_step": int(n * (2 * 501 * 4 + 1)),
+                        "d2h_bytes_per_step": int(n * 501 * 4)},
+                "gpu_launches": launches0, "roofline": roof, "clocks": clk.summary(),
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        rank, world, _ = dist_setup("gloo")
+        run_reference(args, rank, world)
+    else:
+        rank, world, local = dist_setup("nccl")
+        run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

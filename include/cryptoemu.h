@@ -175,6 +175,15 @@ ce_status ce_synchronize(ce_ctx *ctx);
  * call launched (for launch accounting). */
 int ce_last_launch_count(ce_ctx *ctx);
 
+/* Per-kernel timing for measurement: while enabled, every kernel launch of
+ * the gate path is bracketed by CUDA events on its own stream.
+ * ce_profile_read waits for them and returns, per kernel kind (0 = linear
+ * combination + modulus switch, 1 = blind rotation, 2 = extraction + key
+ * switching), the summed milliseconds and the launch count since the last
+ * read. */
+ce_status ce_profile_enable(ce_ctx *ctx, int on);
+ce_status ce_profile_read(ce_ctx *ctx, double *ms, int *launches, int kinds);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,6 +67,8 @@ def lib() -> ctypes.CDLL:
         "ce_set_blind_rotate_config": (i32, [vp, i32, i32]),
         "ce_last_launch_count": (i32, [vp]),
         "ce_synchronize": (i32, [vp]),
+        "ce_profile_enable": (i32, [vp, i32]),
+        "ce_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -275,3 +277,18 @@ def ce_last_launch_count(ctx: Context) -> int:
 
 def ce_synchronize(ctx: Context):
     _check(lib().ce_synchronize(ctx.ptr), "ce_synchronize")
+
+
+KERNEL_KINDS = ["lincomb_modswitch", "blind_rotate", "extract_keyswitch"]
+
+
+def ce_profile_enable(ctx: Context, on: bool = True):
+    _check(lib().ce_profile_enable(ctx.ptr, int(on)), "ce_profile_enable")
+
+
+def ce_profile_read(ctx: Context) -> dict:
+    k = len(KERNEL_KINDS)
+    ms = (ctypes.c_double * k)()
+    cnt = (ctypes.c_int * k)()
+    _check(lib().ce_profile_read(ctx.ptr, ms, cnt, k), "ce_profile_read")
+    return {name: (ms[i], cnt[i]) for i, name in enumerate(KERNEL_KINDS)}

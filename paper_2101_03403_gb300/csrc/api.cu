@@ -98,6 +98,12 @@ struct ce_ctx {
   size_t io_cap = 0;
   int cfg_g = 0, cfg_bps = 0;
   int last_launches = 0;
+  // Optional per-kernel timing: event pairs recorded around each launch on
+  // the launching stream, summed by ce_profile_read.
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Timed { int kind; cudaEvent_t a, b; };
+  std::vector<Timed> timed;
 };
 
 namespace {
@@ -170,6 +176,29 @@ void ks_config(const ce_ctx *ctx, size_t n_out, int *tile, int *jsplit) {
   *jsplit = int(js);
 }
 
+cudaEvent_t take_event(ce_ctx *ctx) {
+  if (!ctx->ev_pool.empty()) {
+    cudaEvent_t e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Records an event pair around `launch` when profiling is on.
+template <class F>
+cudaError_t timed_launch(ce_ctx *ctx, int kind, cudaStream_t st, F launch) {
+  if (!ctx->profile) return launch();
+  cudaEvent_t a = take_event(ctx), b = take_event(ctx);
+  cudaEventRecord(a, st);
+  cudaError_t e = launch();
+  cudaEventRecord(b, st);
+  ctx->timed.push_back({kind, a, b});
+  return e;
+}
+
 // Jobs -> blind rotation -> extraction/key switching on device buffers.
 ce_status run_path(ce_ctx *ctx, Client *cl, int mode, const uint8_t *ops, const uint32_t *a,
                    const uint32_t *b, const uint32_t *c, uint32_t *out, size_t n,
@@ -183,13 +212,17 @@ ce_status run_path(ce_ctx *ctx, Client *cl, int mode, const uint8_t *ops, const 
   ce_status s = ensure_jobs(ctx, jobs);
   if (s != CE_OK) return s;
   int launches = 0;
-  cudaError_t e = launch_lincomb_modswitch(ops, a, b, c, ctx->abar, int(jobs), mode, ctx->err, st);
+  cudaError_t e = timed_launch(ctx, 0, st, [&] {
+    return launch_lincomb_modswitch(ops, a, b, c, ctx->abar, int(jobs), mode, ctx->err, st);
+  });
   if (e != cudaSuccess) return cuda_fail(e, "lincomb_modswitch");
   ++launches;
   int G, blocks;
   br_config(ctx, jobs, &G, &blocks);
-  e = launch_blind_rotate(cl->bsk, ctx->abar, ctx->acc, int(jobs), ctx->tw, ctx->err, G, blocks,
-                          st);
+  e = timed_launch(ctx, 1, st, [&] {
+    return launch_blind_rotate(cl->bsk, ctx->abar, ctx->acc, int(jobs), ctx->tw, ctx->err, G,
+                               blocks, st);
+  });
   if (e != cudaSuccess) return cuda_fail(e, "blind_rotate");
   ++launches;
   int tile, jsplit;
@@ -198,7 +231,9 @@ ce_status run_path(ce_ctx *ctx, Client *cl, int mode, const uint8_t *ops, const 
     e = cudaMemsetAsync(out, 0, n * kLweWords * sizeof(uint32_t), st);
     if (e != cudaSuccess) return cuda_fail(e, "memset");
   }
-  e = launch_extract_keyswitch(ctx->acc, cl->ksk, out, int(n), mode != 0, tile, jsplit, st);
+  e = timed_launch(ctx, 2, st, [&] {
+    return launch_extract_keyswitch(ctx->acc, cl->ksk, out, int(n), mode != 0, tile, jsplit, st);
+  });
   if (e != cudaSuccess) return cuda_fail(e, "extract_keyswitch");
   ++launches;
   ctx->last_launches = launches;
@@ -272,6 +307,11 @@ extern "C" void ce_destroy(ce_ctx *ctx) {
   cudaFree(ctx->io_a);
   cudaFree(ctx->io_b);
   cudaFree(ctx->io_out);
+  for (auto &t : ctx->timed) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   delete ctx;
 }
 
@@ -441,4 +481,33 @@ extern "C" ce_status ce_synchronize(ce_ctx *ctx) {
   cudaError_t e = ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "ce_synchronize");
   return check_device_error(ctx);
+}
+
+extern "C" ce_status ce_profile_enable(ce_ctx *ctx, int on) {
+  if (!ctx) return set_error(CE_EINVAL, "ce_profile_enable: null context");
+  ctx->profile = on != 0;
+  return CE_OK;
+}
+
+extern "C" ce_status ce_profile_read(ce_ctx *ctx, double *ms, int *launches, int kinds) {
+  if (!ctx || !ms || !launches || kinds <= 0)
+    return set_error(CE_EINVAL, "ce_profile_read: bad argument");
+  for (int k = 0; k < kinds; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  for (auto &t : ctx->timed) {
+    cudaError_t e = cudaEventSynchronize(t.b);
+    if (e != cudaSuccess) return cuda_fail(e, "ce_profile_read");
+    float f = 0.f;
+    cudaEventElapsedTime(&f, t.a, t.b);
+    if (t.kind < kinds) {
+      ms[t.kind] += f;
+      launches[t.kind] += 1;
+    }
+    ctx->ev_pool.push_back(t.a);
+    ctx->ev_pool.push_back(t.b);
+  }
+  ctx->timed.clear();
+  return CE_OK;
 }

@@ -154,10 +154,10 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::kRing + G * L::kGate);
   uint32_t *count = reinterpret_cast<uint32_t *>(full + NSLOT);
   volatile int *abort = reinterpret_cast<volatile int *>(count + NSLOT);
-  const int bar = 1 + g;
   const uint64_t *tw_fwd = tw, *tw_inv = tw + 1024;
   constexpr int kChunksPerGate = kLweN * kGadgetL;  // 1500
   constexpr int kWarps = 4 * G;
+  constexpr int kThreads = 128 * G;
 
   const int n_groups = (n_jobs + G - 1) / G;
   const int my_groups =
@@ -196,13 +196,17 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
         acc[kRingN + j] = hi ? kMuEighth : 0u - kMuEighth;
       }
     }
-    ntt::named_bar(bar);
+    ntt::named_bar(1, kThreads);
 
     for (int i = 0; i < kLweN; ++i) {
+      // Every gate of the block runs every step in lockstep (block-wide
+      // barriers keep all warps in the same code region).  A zero rotation
+      // (or an inactive slot) gives D = 0, whose digits are all zero, so the
+      // step adds exactly zero.
       const int rot = active ? __ldg(ab + i) : 0;
       uint32_t w[16];
       uint64_t X[2][8];
-      if (rot != 0) {
+      {
         // w = X^rot ACC_P - ACC_P + decomposition offset, at n = n1 + 64 n2.
         const uint32_t *src = acc + P * kRingN;
         const int kk = rot & (kRingN - 1);
@@ -223,24 +227,22 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
 #pragma unroll 1
       for (int pz = 0; pz < kGadgetL; ++pz, ++chunk) {
         const int slot = chunk % NSLOT;
+        uint64_t v[16], Y[2][8];
+        const int sh = 22 - 10 * pz;
+#pragma unroll
+        for (int n2 = 0; n2 < 16; ++n2)
+          v[n2] = gl::from_i32(int32_t((w[n2] >> sh) & 1023u) - 512);
+        ntt::forward(v, Y, buf, t, 1, kThreads, tw_fwd);
         wait_slot(smem_u32(full + slot), uint32_t(chunk / NSLOT) & 1u, abort, err);
-        if (rot != 0) {
-          uint64_t v[16], Y[2][8];
-          const int sh = 22 - 10 * pz;
+        // X[o] += Y[0] * key(c=0, p, o) + Y[1] * key(c=1, p, o)
+        const uint64_t *key = ring + size_t(slot) * kChunkWords + t;
 #pragma unroll
-          for (int n2 = 0; n2 < 16; ++n2)
-            v[n2] = gl::from_i32(int32_t((w[n2] >> sh) & 1023u) - 512);
-          ntt::forward(v, Y, buf, t, bar, tw_fwd);
-          // X[o] += Y[0] * key(c=0, p, o) + Y[1] * key(c=1, p, o)
-          const uint64_t *key = ring + size_t(slot) * kChunkWords + t;
+        for (int d = 0; d < 8; ++d) {
 #pragma unroll
-          for (int d = 0; d < 8; ++d) {
-#pragma unroll
-            for (int o = 0; o < 2; ++o) {
-              const uint64_t k0 = key[((0 * 2 + o) * 8 + d) * 128];
-              const uint64_t k1 = key[((1 * 2 + o) * 8 + d) * 128];
-              X[o][d] = gl::add(X[o][d], gl::add(gl::mul(Y[0][d], k0), gl::mul(Y[1][d], k1)));
-            }
+          for (int o = 0; o < 2; ++o) {
+            const uint64_t k0 = key[((0 * 2 + o) * 8 + d) * 128];
+            const uint64_t k1 = key[((1 * 2 + o) * 8 + d) * 128];
+            X[o][d] = gl::add(X[o][d], gl::add(gl::mul(Y[0][d], k0), gl::mul(Y[1][d], k1)));
           }
         }
         // Release the slot; the last warp out refills it with chunk + NSLOT.
@@ -258,20 +260,20 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
           }
         }
       }
-      if (rot != 0) {
+      {
         uint64_t v[16];
-        ntt::inverse(X, v, buf, t, bar, tw_inv);
+        ntt::inverse(X, v, buf, t, 1, kThreads, tw_inv);
         uint32_t *dst = acc + P * kRingN + n1;
 #pragma unroll
         for (int n2 = 0; n2 < 16; ++n2) dst[64 * n2] += gl::lift32(v[n2]);
       }
-      ntt::named_bar(bar);
+      ntt::named_bar(1, kThreads);
     }
     if (active) {
       uint32_t *out = acc_out + size_t(job) * 2 * kRingN;
       for (int j = t; j < 2 * kRingN; j += 128) out[j] = acc[j];
     }
-    ntt::named_bar(bar);
+    ntt::named_bar(1, kThreads);
   }
 }
 
@@ -372,7 +374,7 @@ __global__ void __launch_bounds__(128) bsk_to_transform_kernel(const uint32_t *_
     uint64_t v[16], X[2][8];
 #pragma unroll
     for (int n2 = 0; n2 < 16; ++n2) v[n2] = row[n1 + 64 * n2];
-    ntt::forward(v, X, buf, t, 1, tw);
+    ntt::forward(v, X, buf, t, 1, 128, tw);
     uint64_t *dst = out + size_t(blockIdx.x) * kChunkWords;
 #pragma unroll
     for (int o = 0; o < 2; ++o)
@@ -395,15 +397,15 @@ __global__ void __launch_bounds__(128) negacyclic_mul_kernel(const int16_t *__re
 #pragma unroll
   for (int n2 = 0; n2 < 16; ++n2)
     v[n2] = live ? gl::from_i32(dg[size_t(prod) * kRingN + n1 + 64 * n2]) : 0;
-  ntt::forward(v, XD, buf, t, 1, tw);
+  ntt::forward(v, XD, buf, t, 1, 128, tw);
 #pragma unroll
   for (int n2 = 0; n2 < 16; ++n2) v[n2] = live ? k[size_t(prod) * kRingN + n1 + 64 * n2] : 0;
-  ntt::forward(v, XK, buf, t, 1, tw);
+  ntt::forward(v, XK, buf, t, 1, 128, tw);
 #pragma unroll
   for (int q = 0; q < 2; ++q)
 #pragma unroll
     for (int d = 0; d < 8; ++d) XD[q][d] = gl::mul(XD[q][d], XK[q][d]);
-  ntt::inverse(XD, v, buf, t, 1, tw + 1024);
+  ntt::inverse(XD, v, buf, t, 1, 128, tw + 1024);
   if (live) {
 #pragma unroll
     for (int n2 = 0; n2 < 16; ++n2) out[size_t(prod) * kRingN + n1 + 64 * n2] = gl::lift32(v[n2]);

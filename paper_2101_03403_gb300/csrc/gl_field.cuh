@@ -82,6 +82,30 @@ __device__ __forceinline__ uint64_t mul_pow2(uint64_t x, int s) {
   return negate ? neg(r) : r;
 }
 
+// x * 2^s mod p for a runtime shift s in [0, 192) that is the same across
+// the warp: the case branches are uniform, and the shifts are register
+// funnel shifts.  Kept out of line of the unrolled code by the compiler's
+// choice; one copy serves every call site with a warp-uniform shift.
+__device__ __forceinline__ uint64_t mul_pow2_uniform(uint64_t x, int s) {
+  bool negate = false;
+  if (s >= 96) {
+    s -= 96;
+    negate = true;
+  }
+  uint64_t r;
+  if (s == 0) {
+    r = x;
+  } else if (s < 64) {
+    r = reduce128(x >> (64 - s), x << s);
+  } else {
+    const int t = s - 64;
+    const uint64_t y = (t == 0) ? x : reduce128(x >> (64 - t), x << t);
+    const uint64_t lo = y << 32, hi = y >> 32;
+    r = reduce128(hi - (lo < y ? 1ull : 0ull), lo - y);
+  }
+  return negate ? neg(r) : r;
+}
+
 // Signed small integer as a field element.
 __device__ __forceinline__ uint64_t from_i32(int32_t v) {
   return v >= 0 ? static_cast<uint64_t>(v) : kP - static_cast<uint64_t>(-static_cast<int64_t>(v));

@@ -30,8 +30,10 @@ namespace ntt {
 constexpr int kRow = 65;                 // padded row of the transpose buffer
 constexpr int kBufWords = 2 * 16 * kRow; // uint64 words per 128-thread group
 
-__device__ __forceinline__ void named_bar(int id) {
-  asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory");
+// Barrier `id` over `count` threads (all groups of a block share one barrier
+// so that every warp of the block runs the same code region at a time).
+__device__ __forceinline__ void named_bar(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 __host__ __device__ constexpr int bitrev(int k, int bits) {
@@ -82,23 +84,23 @@ __device__ __forceinline__ void fwd_phase_a(uint64_t (&v)[16], uint64_t *buf, in
   for (int k2 = 0; k2 < 16; ++k2) col[k2 * kRow] = gl::mul(v[k2], __ldg(tw_fwd + k2 * 64 + n1));
 }
 
-// Phase C1 for warp WG of the group: lane -> (P, k2) = (lane >> 4, lane & 15),
-// a in {2 WG, 2 WG + 1} (warp-uniform, so the twiddle shifts are constants).
-template <int WG>
-__device__ __forceinline__ void fwd_phase_c1(uint64_t *buf, int lane, int bar) {
+// Phase C1 for warp wg of the group: lane -> (P, k2) = (lane >> 4, lane & 15),
+// a in {2 wg, 2 wg + 1}.  a is warp-uniform, so the shift of the twiddle
+// 8^(a c) is the same across the warp (uniform branches, one code copy).
+__device__ __forceinline__ void fwd_phase_c1(uint64_t *buf, int wg, int lane, int bar, int nthr) {
   uint64_t *row = buf + ((lane >> 4) * 16 + (lane & 15)) * kRow;
   uint64_t u[2][8];
 #pragma unroll
   for (int j = 0; j < 2; ++j)
 #pragma unroll
-    for (int b = 0; b < 8; ++b) u[j][b] = row[2 * WG + j + 8 * b];
-  named_bar(bar);  // every read of this phase precedes every write
+    for (int b = 0; b < 8; ++b) u[j][b] = row[2 * wg + j + 8 * b];
+  named_bar(bar, nthr);  // every read of this phase precedes every write
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     dft<8, 24>(u[j]);
-    const int a = 2 * WG + j;
+    const int a = 2 * wg + j;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) row[c * 8 + a] = gl::mul_pow2(u[j][c], (3 * a * c) % 192);
+    for (int c = 0; c < 8; ++c) row[c * 8 + a] = gl::mul_pow2_uniform(u[j][c], (3 * a * c) % 192);
   }
 }
 
@@ -117,18 +119,13 @@ __device__ __forceinline__ void fwd_phase_c2(uint64_t (&X)[2][8], const uint64_t
 // Forward transform of two polynomials; v holds the phase-A inputs of this
 // thread (clobbered), X receives the eight positions of each polynomial.
 __device__ __forceinline__ void forward(uint64_t (&v)[16], uint64_t (&X)[2][8], uint64_t *buf,
-                                        int t, int bar, const uint64_t *__restrict__ tw_fwd) {
-  named_bar(bar);  // the buffer is free
+                                        int t, int bar, int nthr,
+                                        const uint64_t *__restrict__ tw_fwd) {
+  named_bar(bar, nthr);  // the buffer is free
   fwd_phase_a(v, buf, t, tw_fwd);
-  named_bar(bar);
-  const int lane = t & 31;
-  switch (t >> 5) {
-    case 0: fwd_phase_c1<0>(buf, lane, bar); break;
-    case 1: fwd_phase_c1<1>(buf, lane, bar); break;
-    case 2: fwd_phase_c1<2>(buf, lane, bar); break;
-    default: fwd_phase_c1<3>(buf, lane, bar); break;
-  }
-  named_bar(bar);
+  named_bar(bar, nthr);
+  fwd_phase_c1(buf, t >> 5, t & 31, bar, nthr);
+  named_bar(bar, nthr);
   fwd_phase_c2(X, buf, t);
 }
 
@@ -145,21 +142,21 @@ __device__ __forceinline__ void inv_phase_c2(uint64_t (&X)[2][8], uint64_t *buf,
   }
 }
 
-template <int WG>
-__device__ __forceinline__ void inv_phase_c1(uint64_t *buf, int lane, int bar) {
+__device__ __forceinline__ void inv_phase_c1(uint64_t *buf, int wg, int lane, int bar, int nthr) {
   uint64_t *row = buf + ((lane >> 4) * 16 + (lane & 15)) * kRow;
   uint64_t u[2][8];
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
-    const int a = 2 * WG + j;
+    const int a = 2 * wg + j;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) u[j][c] = gl::mul_pow2(row[c * 8 + a], (192 - (3 * a * c) % 192) % 192);
+    for (int c = 0; c < 8; ++c)
+      u[j][c] = gl::mul_pow2_uniform(row[c * 8 + a], (192 - (3 * a * c) % 192) % 192);
   }
-  named_bar(bar);
+  named_bar(bar, nthr);
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     dft<8, 168>(u[j]);
-    const int a = 2 * WG + j;
+    const int a = 2 * wg + j;
 #pragma unroll
     for (int b = 0; b < 8; ++b) row[a + 8 * b] = u[j][b];
   }
@@ -179,18 +176,13 @@ __device__ __forceinline__ void inv_phase_a(uint64_t (&v)[16], const uint64_t *b
 // Inverse transform: X (clobbered) holds this thread's positions of both
 // polynomials; v receives x_P[n1 + 64 n2] for (P, n1) = (t >> 6, t & 63).
 __device__ __forceinline__ void inverse(uint64_t (&X)[2][8], uint64_t (&v)[16], uint64_t *buf,
-                                        int t, int bar, const uint64_t *__restrict__ tw_inv) {
-  named_bar(bar);
+                                        int t, int bar, int nthr,
+                                        const uint64_t *__restrict__ tw_inv) {
+  named_bar(bar, nthr);
   inv_phase_c2(X, buf, t);
-  named_bar(bar);
-  const int lane = t & 31;
-  switch (t >> 5) {
-    case 0: inv_phase_c1<0>(buf, lane, bar); break;
-    case 1: inv_phase_c1<1>(buf, lane, bar); break;
-    case 2: inv_phase_c1<2>(buf, lane, bar); break;
-    default: inv_phase_c1<3>(buf, lane, bar); break;
-  }
-  named_bar(bar);
+  named_bar(bar, nthr);
+  inv_phase_c1(buf, t >> 5, t & 31, bar, nthr);
+  named_bar(bar, nthr);
   inv_phase_a(v, buf, t, tw_inv);
 }
 

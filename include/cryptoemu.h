@@ -175,6 +175,24 @@ ce_status ce_synchronize(ce_ctx *ctx);
  * call launched (for launch accounting). */
 int ce_last_launch_count(ce_ctx *ctx);
 
+/* The paper has no counterpart to this call.  Same as ce_gates_batch_device
+ * (same kernels, same results) but it allocates no device memory: for
+ * callers that cannot let the library call cudaMalloc, e.g. a serving loop
+ * that must not take cudaMalloc's implicit device-wide synchronisation, or a
+ * process whose device memory another allocator has reserved up front.  Its
+ * scratch is a fixed area inside the library's device image (about 2.3 MB
+ * on every GPU that loads the library, held until the process exits), so a
+ * call takes at most 256 gates (CE_EINVAL above that).  The first call on a
+ * device looks up that area's address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  Every call reuses the same area:
+ * calls whose work overlaps on the GPU (different streams, different
+ * contexts) race and corrupt each other's results, so serialise them.  No
+ * scratch word needs to start at zero: each call writes everything it reads.
+ * The keys are the client's keys held by the context (admitted earlier). */
+ce_status ce_gates_batch_device_noalloc(ce_ctx *ctx, int client, const uint8_t *d_ops,
+                                        const uint32_t *d_a, const uint32_t *d_b,
+                                        uint32_t *d_out, size_t n, void *cuda_stream);
+
 /* Per-kernel timing for measurement: while enabled, every kernel launch of
  * the gate path is bracketed by CUDA events on its own stream.
  * ce_profile_read waits for them and returns, per kernel kind (0 = linear

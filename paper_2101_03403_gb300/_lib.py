@@ -62,6 +62,7 @@ def lib() -> ctypes.CDLL:
         "ce_gate": (i32, [vp, i32, i32, vp, vp, vp]),
         "ce_gates_batch": (i32, [vp, i32, vp, vp, vp, vp, sz]),
         "ce_gates_batch_device": (i32, [vp, i32, vp, vp, vp, vp, sz, vp]),
+        "ce_gates_batch_device_noalloc": (i32, [vp, i32, vp, vp, vp, vp, sz, vp]),
         "ce_mux_batch_device": (i32, [vp, i32, vp, vp, vp, vp, sz, vp]),
         "ce_negacyclic_mul_device": (i32, [vp, vp, vp, vp, sz, vp]),
         "ce_set_blind_rotate_config": (i32, [vp, i32, i32]),
@@ -254,6 +255,15 @@ def ce_gates_batch_device(ctx: Context, client: int, d_ops, d_a, d_b, d_out, n: 
                           stream=None):
     _check(lib().ce_gates_batch_device(ctx.ptr, client, _addr(d_ops), _addr(d_a), _addr(d_b),
                                        _addr(d_out), n, _stream(stream)), "ce_gates_batch_device")
+
+
+def ce_gates_batch_device_noalloc(ctx: Context, client: int, d_ops, d_a, d_b, d_out, n: int,
+                                  stream=None):
+    """ce_gates_batch_device without any device allocation (at most 256 gates;
+    scratch is a fixed area of the library's device image shared by all calls)."""
+    _check(lib().ce_gates_batch_device_noalloc(ctx.ptr, client, _addr(d_ops), _addr(d_a),
+                                               _addr(d_b), _addr(d_out), n, _stream(stream)),
+           "ce_gates_batch_device_noalloc")
 
 
 def ce_mux_batch_device(ctx: Context, client: int, d_a, d_b, d_c, d_out, n: int, stream=None):

@@ -511,3 +511,28 @@ extern "C" ce_status ce_profile_read(ce_ctx *ctx, double *ms, int *launches, int
   ctx->timed.clear();
   return CE_OK;
 }
+
+namespace ce {
+
+// Keys and launch shapes of the gate path for entry points defined in other
+// translation units.  Allocates nothing.
+ce_status gate_path_resources(ce_ctx *ctx, int client, GatePathResources *out) {
+  if (!ctx || !out) return set_error(CE_EINVAL, "null context");
+  Client *cl = find_client(ctx, client);
+  if (!cl) return set_error(CE_ENOTFOUND, "unknown client");
+  out->bsk = cl->bsk;
+  out->ksk = cl->ksk;
+  out->tw = ctx->tw;
+  out->err = ctx->err;
+  out->device = ctx->device;
+  out->stream = ctx->stream;
+  return CE_OK;
+}
+
+void gate_path_shape(const ce_ctx *ctx, size_t jobs, size_t n_out, int *G, int *blocks,
+                     int *tile, int *jsplit) {
+  br_config(ctx, jobs, G, blocks);
+  ks_config(ctx, n_out, tile, jsplit);
+}
+
+}  // namespace ce

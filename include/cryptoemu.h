@@ -175,6 +175,36 @@ ce_status ce_synchronize(ce_ctx *ctx);
  * call launched (for launch accounting). */
 int ce_last_launch_count(ce_ctx *ctx);
 
+/* ------------------------------------------------------ functional units --- */
+
+/* Functional units of the emulator (§5 "Data Processing Units", §6
+ * "Conditional Flags") as netlists of bootstrapped gates.  Inputs: a[w]
+ * then b[w] (bit 0 first); CSEL: rn[w], rm[w], N, Z, C, V.  Outputs: w bits;
+ * CMP: N, Z, C, V of a - b.  cond (CSEL only): 0 EQ, 1 NE, 2 CS, 3 CC, 4 MI,
+ * 5 PL, 6 VS, 7 VC, 8 HI, 9 LS, 10 GE, 11 LT, 12 GT, 13 LE. */
+typedef enum {
+    CE_U_ADD = 0,         /* Kogge-Stone parallel-prefix adder (§5 "Adder") */
+    CE_U_ADD_RIPPLE = 1,  /* ripple-carry adder */
+    CE_U_SUB = 2,         /* a + NOT b + 1 (§5 "Subtractor") */
+    CE_U_AND = 3,         /* bitwise AND (§5 "Bitwise operations") */
+    CE_U_ORR = 4,         /* bitwise OR */
+    CE_U_LSL = 5,         /* a << (b mod w), barrel shifter of MUX stages (§5 "Shifter") */
+    CE_U_MUL = 6,         /* (a * b) mod 2^w, array multiplier (§5 "Multiplier") */
+    CE_U_UDIV = 7,        /* a / b (0 for b = 0), non-restoring (§5 "Divider") */
+    CE_U_CMP = 8,         /* NZCV flags of a - b (§6 "Conditional Flags") */
+    CE_U_CSEL = 9         /* cond(NZCV) ? rn : rm */
+} ce_unit;
+
+/* Shape of a unit's netlist for width w (a power of two, 2..32). */
+ce_status ce_unit_info(int unit, int cond, int width, int *n_inputs, int *n_outputs,
+                       int *n_gates, int *n_bootstraps, int *depth);
+/* The netlist as int32 words: n_inputs, n_wires, depth, n_gates, n_outputs;
+ * per gate (ordered by level): op (0..9 gate, 10 MUX), a.wire, a.neg,
+ * b.wire, b.neg, c.wire, c.neg (MUX selector a: a ? b : c), out, level; per
+ * output: wire, neg.  Wire -1 is the constant false (negated: true).  With
+ * buf NULL only *used is set. */
+ce_status ce_unit_netlist(int unit, int cond, int width, int32_t *buf, size_t cap, size_t *used);
+
 /* The paper has no counterpart to this call.  Same as ce_gates_batch_device
  * (same kernels, same results) but it allocates no device memory: for
  * callers that cannot let the library call cudaMalloc, e.g. a serving loop

@@ -69,6 +69,9 @@ def lib() -> ctypes.CDLL:
         "ce_last_launch_count": (i32, [vp]),
         "ce_synchronize": (i32, [vp]),
         "ce_profile_enable": (i32, [vp, i32]),
+        "ce_unit_info": (i32, [i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                               ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "ce_unit_netlist": (i32, [i32, i32, i32, vp, sz, ctypes.POINTER(sz)]),
         "ce_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), i32]),
     }
     for name, (res, args) in sig.items():
@@ -302,3 +305,41 @@ def ce_profile_read(ctx: Context) -> dict:
     cnt = (ctypes.c_int * k)()
     _check(lib().ce_profile_read(ctx.ptr, ms, cnt, k), "ce_profile_read")
     return {name: (ms[i], cnt[i]) for i, name in enumerate(KERNEL_KINDS)}
+
+
+UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "CSEL"]
+UNIT_ID = {u: i for i, u in enumerate(UNITS)}
+
+
+def _unit(u) -> int:
+    return UNIT_ID[u] if isinstance(u, str) else int(u)
+
+
+def ce_unit_info(unit, cond: int = 0, width: int = 16) -> dict:
+    v = [ctypes.c_int() for _ in range(5)]
+    _check(lib().ce_unit_info(_unit(unit), cond, width, *[ctypes.byref(x) for x in v]),
+           "ce_unit_info")
+    return dict(zip(["n_inputs", "n_outputs", "n_gates", "n_bootstraps", "depth"],
+                    [x.value for x in v]))
+
+
+def ce_unit_netlist(unit, cond: int = 0, width: int = 16) -> dict:
+    """The library's netlist: gates as (op, a, b, c, out, level) with refs
+    (wire, negated), ordered by level."""
+    used = ctypes.c_size_t()
+    _check(lib().ce_unit_netlist(_unit(unit), cond, width, None, 0, ctypes.byref(used)),
+           "ce_unit_netlist")
+    buf = np.zeros(used.value, np.int32)
+    _check(lib().ce_unit_netlist(_unit(unit), cond, width, buf.ctypes.data, used.value,
+                                 ctypes.byref(used)), "ce_unit_netlist")
+    n_in, n_wires, depth, n_g, n_o = (int(x) for x in buf[:5])
+    g = buf[5:5 + 9 * n_g].reshape(n_g, 9)
+    gates = []
+    for r in g:
+        op = int(r[0])
+        c = (int(r[5]), bool(r[6])) if op == 10 else (-1, False)
+        gates.append((op, (int(r[1]), bool(r[2])), (int(r[3]), bool(r[4])), c, int(r[7]),
+                      int(r[8])))
+    o = buf[5 + 9 * n_g:].reshape(n_o, 2)
+    return {"n_inputs": n_in, "n_wires": n_wires, "depth": depth, "gates": gates,
+            "outputs": [(int(x), bool(y)) for x, y in o]}

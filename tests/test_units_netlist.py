@@ -1,0 +1,117 @@
+"""Functional-unit netlists: the oracle's construction (oracle/netlists.py)
+checked exhaustively against ARMv8 semantics at width 8 and on random
+16-bit operands, gate counts against the paper's structure, and the
+library's independently built netlists equal to the oracle's gate for gate."""
+import numpy as np
+import pytest
+
+from oracle import netlists as NL
+
+UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP"]
+
+
+def eval_vec(net, inputs):
+    """Plaintext evaluation on arrays of input bits (one array per input)."""
+    n = len(inputs[0])
+    val = [np.asarray(x, np.uint8) for x in inputs] + [None] * (len(net.levels) - net.n_inputs)
+    zero = np.zeros(n, np.uint8)
+
+    def rd(r):
+        v = zero if r[0] < 0 else val[r[0]]
+        return 1 - v if r[1] else v
+
+    for op, a, b, c, out, _ in net.by_level():
+        if op == NL.MUX:
+            val[out] = np.where(rd(a) == 1, rd(b), rd(c)).astype(np.uint8)
+        else:
+            val[out] = np.asarray(NL.GATE_FN[op](rd(a).astype(np.int64), rd(b).astype(np.int64)),
+                                  np.uint8)
+    return [rd(r) for r in net.outputs]
+
+
+def check_unit(unit, w, a, b, cond=0, nzcv=None):
+    net = NL.build(unit, w, cond)
+    ins = [(a >> i) & 1 for i in range(w)] + [(b >> i) & 1 for i in range(w)]
+    if unit == "CSEL":
+        ins += [(nzcv >> i) & 1 for i in range(4)]
+    outs = eval_vec(net, ins)
+    if unit == "CMP":
+        exp = np.array([NL.armv8(unit, int(x), int(y), w) for x, y in zip(a, b)])
+        for k in range(4):
+            assert (outs[k] == exp[:, k]).all(), (unit, k)
+    else:
+        got = sum(outs[i].astype(np.int64) << i for i in range(w))
+        if unit == "CSEL":
+            exp = np.array([NL.armv8(unit, int(x), int(y), w, cond, int(f))
+                            for x, y, f in zip(a, b, nzcv)])
+        else:
+            exp = np.array([NL.armv8(unit, int(x), int(y), w) for x, y in zip(a, b)])
+        bad = np.nonzero(got != exp)[0]
+        assert len(bad) == 0, (unit, int(a[bad[0]]), int(b[bad[0]]), int(got[bad[0]]))
+
+
+@pytest.mark.parametrize("unit", UNITS)
+def test_exhaustive_width8(unit):
+    a, b = np.meshgrid(np.arange(256), np.arange(256))
+    check_unit(unit, 8, a.ravel(), b.ravel())
+
+
+@pytest.mark.parametrize("unit", UNITS)
+def test_random_width16(unit):
+    rng = np.random.default_rng(16)
+    a = rng.integers(0, 1 << 16, 4000)
+    b = rng.integers(0, 1 << 16, 4000)
+    b[:40] = 0
+    b[40:80] = a[40:80]
+    a[80:120] = 0xFFFF
+    check_unit(unit, 16, a, b)
+
+
+@pytest.mark.parametrize("cond", range(14))
+def test_csel_all_conditions(cond):
+    rng = np.random.default_rng(cond)
+    n = 512
+    check_unit("CSEL", 8, rng.integers(0, 256, n), rng.integers(0, 256, n), cond,
+               np.tile(np.arange(16), n // 16))
+
+
+def test_structure_matches_the_paper():
+    add = NL.build("ADD", 16)
+    # §5 "Adder": 16 get_gp (32 gates) + 15/14/12/8 span operators of 3 gates
+    # + 15 sum XORs (bit 0 is p_0).  The paper runs 4 carry levels of 2
+    # gate levels each in lock step (depth 10); as-soon-as-possible levels
+    # let each span start as soon as its inputs exist (depth 9).
+    assert len(add.gates) == 32 + 3 * (15 + 14 + 12 + 8) + 15
+    assert add.depth == 9
+    lsl = NL.build("LSL", 16)
+    # §5 "Shifter": 4 stages x 16 MUX
+    assert len(lsl.gates) == 64 and lsl.depth == 4 and lsl.bootstraps == 128
+    mul = NL.build("MUL", 16)
+    assert sum(1 for g in mul.gates if g[5] == 1) == 136      # partial products
+    cmp_ = NL.build("CMP", 16)
+    sub = NL.build("SUB", 16)
+    # §6: Z by a 15-OR tree, V by 5 gates
+    assert len(cmp_.gates) == len(sub.gates) + 15 + 5
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2101_03403_gb300 import build
+    build.build()
+    import paper_2101_03403_gb300 as ce
+    return ce
+
+
+@pytest.mark.parametrize("unit", UNITS + ["CSEL"])
+@pytest.mark.parametrize("w", [8, 16])
+def test_library_netlist_equals_oracle(lib, unit, w):
+    conds = range(14) if unit == "CSEL" else [0]
+    for cond in conds:
+        mine = NL.build(unit, w, cond)
+        theirs = lib.ce_unit_netlist(unit, cond, w)
+        assert theirs["n_inputs"] == mine.n_inputs
+        assert theirs["depth"] == mine.depth
+        assert theirs["gates"] == mine.by_level(), (unit, w, cond)
+        assert theirs["outputs"] == list(mine.outputs)
+        info = lib.ce_unit_info(unit, cond, w)
+        assert info["n_bootstraps"] == mine.bootstraps

@@ -2,19 +2,22 @@
 """Benchmark of the GB300 gate-bootstrapping path.
 
 Metric: bootstrapped gates per second on one GB300 (exact: every output is
-the bit-exact result of the plain definition).  A step is one pass of the
-whole hot path (linear combination + modulus switch, blind rotation, sample
-extraction + key switching) over one level of 8192 independent gates: the
-first level of the 16-bit parallel-prefix adder (one AND and one XOR per bit,
-§5 "Adder", Stage 1) for 256 encrypted operand pairs.  Inputs are synthetic
-and seeded (fresh encryptions of uniform random bits under keys generated
-from seed 20210103).
+the bit-exact result of the plain definition), plus encrypted 16-bit ADD and
+MUL latency percentiles.  A step is one evaluation of the 16-bit
+parallel-prefix adder (§5 "Adder": 194 bootstrapped gates, 9 levels) on 256
+encrypted operand pairs drawn uniformly from [0, 2^16): every level of all
+256 additions is one pass of the whole hot path (linear combination +
+modulus switch, blind rotation, sample extraction + key switching), i.e.
+49,664 bootstraps per step.  MUL latency: the array multiplier on 64 pairs.
+Inputs are synthetic and seeded (fresh encryptions under keys generated from
+seed 20210103).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 `value` uses device-resident inputs (device-side time of K steps, L2 flushed
-between steps); `e2e` runs the same work through the host-buffer C-ABI call
-(ce_gates_batch) with the host<->device copies inside the timed region.
+between steps); `e2e` runs the same steps through the same public call
+(ce_unit_eval_device) with the copy of the step's inputs from pinned host
+memory and of its results back to the host inside the timed region.
 `--impl reference` times the plain CPU oracle (test infrastructure, used here
 only as the reference arm) on a bounded sample of the same workload.
 Under torchrun every rank evaluates its own batch (independent gates, no
@@ -38,7 +41,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 SEED = 20210103
-N_GATES = 8192
 METRIC = "bootstrapped gates/s on 1 GB300 (exact)"
 UNIT = "gates/s"
 # Algorithmic work of one bootstrap, counted as 64-bit modular multiplications
@@ -52,6 +54,7 @@ INT32_OPS_PER_S = 152 * 64 * 2.07e9
 OPS_PER_MODMUL = 16
 PEAK_GMODMUL = INT32_OPS_PER_S / OPS_PER_MODMUL / 1e9
 KERNEL_SOURCES = ["bootstrap_kernels.cu", "ntt_pair.cuh", "gl_field.cuh"]
+N_PAIRS = 256
 
 
 def parse():
@@ -60,7 +63,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--gates", type=int, default=N_GATES)
+    ap.add_argument("--pairs", type=int, default=256, help="ADD operand pairs per step")
     return ap.parse_args()
 
 
@@ -143,10 +146,16 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ oracle ---
+_ORACLE_KEYS = None
+
+
 def oracle_sample(n_gates: int, threads: int):
     """Time the plain CPU oracle on n_gates gates of the same workload."""
+    global _ORACLE_KEYS
     from oracle import oracle as O
-    keys = O.keygen(O.GATE_PARAMS, SEED)
+    if _ORACLE_KEYS is None:
+        _ORACLE_KEYS = O.keygen(O.GATE_PARAMS, SEED)
+    keys = _ORACLE_KEYS
     rng = np.random.default_rng(SEED)
     bits = rng.integers(0, 2, (n_gates, 2))
     p = O.GATE_PARAMS
@@ -175,14 +184,15 @@ def run_reference(args, rank: int, world: int):
         vals.append(oracle_sample(per_step, cores))
         t_all += time.perf_counter() - t0
     value = per_step * args.steps / t_all
-    sample = f"{per_step} gates (AND/XOR) of the {args.gates}-gate level per step, one gate per core"
+    sample = f"{per_step} bootstrapped gates (AND/XOR of the adder's first level) per step, one per core"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_all / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic (seeded encryptions of uniform bits)",
-            "config": {"workload": f"adder level 1: {args.gates} bootstrapped AND/XOR gates "
-                                   "(256 x 16-bit operand pairs), n=500 N=1024 l=3 Bg=2^10 t=8",
+            "config": {"workload": f"16-bit Kogge-Stone ADD on {args.pairs} encrypted operand "
+                                   "pairs, level-batched (n=500 N=1024 l=3 Bg=2^10 t=8); the "
+                                   "oracle times a sample of its gates",
                        "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
@@ -199,9 +209,9 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+def recorded_traffic(kernel: str, launches_per_step=None):
+    """DRAM bytes per launch of the bench workload from the committed ncu
+    summary, if it was taken on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path)).get(kernel)
@@ -212,6 +222,21 @@ def recorded_traffic(kernel: str):
     return rec.get("dram_bytes_per_launch")
 
 
+def encrypt_operands(ce, sk, a, b, seed):
+    """[n][32][501]: bits of a then bits of b, each a fresh encryption."""
+    n = len(a)
+    out = np.zeros((n, 32, 501), np.uint32)
+    for i in range(n):
+        for j in range(16):
+            out[i, j] = ce.ce_encrypt_bit(sk, int(a[i] >> j) & 1, seed, 32 * i + j)
+            out[i, 16 + j] = ce.ce_encrypt_bit(sk, int(b[i] >> j) & 1, seed, 32 * i + 16 + j)
+    return out
+
+
+def decrypt_word(ce, sk, bits) -> int:
+    return sum(ce.ce_decrypt_bit(sk, bits[j]) << j for j in range(16))
+
+
 def run_ours(args, rank: int, world: int, local: int):
     import torch
 
@@ -220,71 +245,78 @@ def run_ours(args, rank: int, world: int, local: int):
     b.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    n = args.gates
+    n = args.pairs
     sk = ce.ce_secret_keygen(SEED)
     ck = ce.ce_cloud_keygen(sk, SEED)
     stream = torch.cuda.current_stream(dev)
     ctx = ce.ce_create(local, 0, stream)
     cid = ce.ce_client_admit(ctx, ck)
+    gates_per_add = ce.ce_unit_info("ADD")["n_bootstraps"]
+    boots = n * gates_per_add
 
     rng = np.random.default_rng(SEED + rank)
-    bits = rng.integers(0, 2, (n, 2))
-    ca = np.stack([ce.ce_encrypt_bit(sk, int(v), 31 + 2 * rank, i) for i, v in enumerate(bits[:, 0])])
-    cb = np.stack([ce.ce_encrypt_bit(sk, int(v), 32 + 2 * rank, i) for i, v in enumerate(bits[:, 1])])
-    ops = np.tile(np.array([1, 3], np.uint8), n // 2 + 1)[:n]        # AND, XOR per bit
-    d_ops = torch.from_numpy(ops).to(dev)
-    d_a = torch.from_numpy(ca.view(np.int32)).to(dev)
-    d_b = torch.from_numpy(cb.view(np.int32)).to(dev)
-    d_out = torch.empty((n, 501), dtype=torch.int32, device=dev)
+    a = rng.integers(0, 1 << 16, n)
+    bb = rng.integers(0, 1 << 16, n)
+    host_in = encrypt_operands(ce, sk, a, bb, 31 + rank)
+    d_in = torch.from_numpy(host_in.view(np.int32)).to(dev)
+    d_out = torch.empty((n, 16, 501), dtype=torch.int32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # > 129 MB L2
 
-    def step():
-        ce.ce_gates_batch_device(ctx, cid, d_ops, d_a, d_b, d_out, n, stream)
+    def step(profiled: bool):
+        ce.ce_profile_enable(ctx, profiled)
+        ce.ce_unit_eval_device(ctx, cid, "ADD", d_in, d_out, n, 0, stream)
 
     for _ in range(max(args.warmup, 3)):
-        step()
+        step(True)
+    step(False)                                   # captures the graph
     ce.ce_synchronize(ctx)
+    ce.ce_profile_read(ctx)
 
-    # correctness guard on the measured output: decrypt a sample
-    out = d_out.cpu().numpy().view(np.uint32)
-    truth = np.where(ops == 1, bits[:, 0] & bits[:, 1], bits[:, 0] ^ bits[:, 1])
-    for i in rng.choice(n, 64, replace=False):
-        assert ce.ce_decrypt_bit(sk, out[i]) == truth[i], "wrong gate output"
+    out = d_out.cpu().numpy().view(np.uint32)     # correctness guard on the measured output
+    for i in rng.choice(n, 16, replace=False):
+        assert decrypt_word(ce, sk, out[i]) == (int(a[i]) + int(bb[i])) & 0xFFFF, "wrong sum"
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ce.ce_profile_enable(ctx, True)
-    launches0 = 0
+    launches = 0
     with ClockSampler(local) as clk:
         barrier(world)
         torch.cuda.synchronize(dev)
         for k in range(args.steps):
-            flush.zero_()                      # outside the per-step events
+            flush.zero_()                         # outside the per-step events
             starts[k].record(stream)
-            step()
-            launches0 += ce.ce_last_launch_count(ctx)
+            step(True)                            # eager, per-kernel events on
+            launches += ce.ce_last_launch_count(ctx)
             ends[k].record(stream)
         torch.cuda.synchronize(dev)
         barrier(world)
     ce.ce_synchronize(ctx)
     prof = ce.ce_profile_read(ctx)
     ce.ce_profile_enable(ctx, False)
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    step_ms = [st.elapsed_time(en) for st, en in zip(starts, ends)]
     total_ms = max_over_ranks(sum(step_ms), world, dev)
-    value = weak_scaling_value(n, args.steps, world, total_ms)
+    value = weak_scaling_value(boots, args.steps, world, total_ms)
 
-    # end to end through the host-buffer call, copies included
-    pin_ops = torch.from_numpy(ops).pin_memory()
-    pin_a = torch.from_numpy(ca).pin_memory()
-    pin_b = torch.from_numpy(cb).pin_memory()
-    pin_out = torch.empty((n, 501), dtype=torch.int32).pin_memory()
-    lib = ce.lib()
+    # the same steps replayed as the captured CUDA graph of the unit
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(args.steps):
+        step(False)
+    g1.record(stream)
+    torch.cuda.synchronize(dev)
+    graph_value = boots * args.steps / (g0.elapsed_time(g1) / 1e3)
+
+    # end to end: pinned host inputs -> device -> unit -> host, per step
+    pin_in = torch.from_numpy(host_in.view(np.int32)).pin_memory()
+    pin_out = torch.empty((n, 16, 501), dtype=torch.int32).pin_memory()
+    e2e_in = torch.empty_like(d_in)
+    e2e_out = torch.empty_like(d_out)
 
     def e2e_step():
-        r = lib.ce_gates_batch(ctx.ptr, cid, pin_ops.data_ptr(), pin_a.data_ptr(), pin_b.data_ptr(),
-                               pin_out.data_ptr(), n)
-        if r != 0:
-            raise RuntimeError(ce.ce_last_error())
+        e2e_in.copy_(pin_in, non_blocking=True)
+        ce.ce_unit_eval_device(ctx, cid, "ADD", e2e_in, e2e_out, n, 0, stream)
+        pin_out.copy_(e2e_out, non_blocking=True)
+        stream.synchronize()
 
     e2e_step()
     barrier(world)
@@ -292,40 +324,70 @@ def run_ours(args, rank: int, world: int, local: int):
     for _ in range(args.steps):
         e2e_step()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
-    e2e_val = n * args.steps * world / e2e_s
-    assert (pin_out.numpy().view(np.uint32) == out).all(), "e2e output differs"
+    e2e_val = boots * args.steps * world / e2e_s
+    assert (pin_out.numpy() == d_out.cpu().numpy()).all(), "e2e output differs"
+
+    # 16-bit MUL latency on 64 pairs (array multiplier)
+    mul_n = 64
+    ma, mb = rng.integers(0, 1 << 16, mul_n), rng.integers(0, 1 << 16, mul_n)
+    d_min = torch.from_numpy(encrypt_operands(ce, sk, ma, mb, 77).view(np.int32)).to(dev)
+    d_mout = torch.empty((mul_n, 16, 501), dtype=torch.int32, device=dev)
+    ce.ce_unit_eval_device(ctx, cid, "MUL", d_min, d_mout, mul_n, 0, stream)
+    torch.cuda.synchronize(dev)
+    mul_ms = []
+    for _ in range(max(3, args.steps)):
+        m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        m0.record(stream)
+        ce.ce_unit_eval_device(ctx, cid, "MUL", d_min, d_mout, mul_n, 0, stream)
+        m1.record(stream)
+        torch.cuda.synchronize(dev)
+        mul_ms.append(m0.elapsed_time(m1))
+    mo = d_mout.cpu().numpy().view(np.uint32)
+    for i in range(4):
+        assert decrypt_word(ce, sk, mo[i]) == (int(ma[i]) * int(mb[i])) & 0xFFFF, "wrong product"
+    mul_boots = mul_n * ce.ce_unit_info("MUL")["n_bootstraps"]
 
     br_ms, br_launches = prof["blind_rotate"]
-    br_avg = br_ms / max(br_launches, 1)
-    achieved = n * MODMUL_PER_GATE / (br_avg / 1e3) / 1e9
+    achieved = boots * args.steps * MODMUL_PER_GATE / (br_ms / 1e3) / 1e9
     roof = {"kernel": "blind_rotate", "bound": "alu", "achieved": achieved,
             "peak": PEAK_GMODMUL, "unit": "Gmodmul/s", "frac": achieved / PEAK_GMODMUL,
-            "traffic": recorded_traffic("blind_rotate"),
+            "traffic": recorded_traffic("blind_rotate", args.steps and br_launches / args.steps),
             "peak_note": "derived: 152 SMs x 64 INT32 lanes x 2.07 GHz / 16 ops per modmul",
-            "kernel_ms": {k: v[0] / max(v[1], 1) for k, v in prof.items()}}
+            "launches_per_step": br_launches / args.steps,
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
+
+    def pct(xs, q):
+        return float(np.percentile(np.array(xs), q))
 
     cpu = None
     if rank == 0 and world == 1:
         cores = cpu_cores()
         g = 2 * cores
         cpu = {"value": oracle_sample(g, cores), "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{g} gates (AND/XOR) of the {n}-gate level, one gate per thread"}
+               "sample": f"{g} bootstrapped gates (AND/XOR of the adder's first level), "
+                         "one gate per thread"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-                "data": "synthetic (seeded encryptions of uniform bits)",
-                "config": {"workload": f"adder level 1: {n} bootstrapped AND/XOR gates "
-                                       "(256 x 16-bit operand pairs), n=500 N=1024 l=3 "
-                                       "Bg=2^10 t=8", "gates_per_step_per_gpu": n,
+                "data": "synthetic (seeded encryptions of uniform 16-bit operands)",
+                "config": {"workload": f"16-bit Kogge-Stone ADD on {n} encrypted operand pairs, "
+                                       "level-batched (n=500 N=1024 l=3 Bg=2^10 t=8)",
+                           "bootstraps_per_step": boots, "levels": 9,
                            "l2": "flushed between steps (256 MB write)",
-                           "parallelism": f"independent batches x{world}"},
+                           "parallelism": f"independent batches x{world}",
+                           "graph_replay_gates_per_s": graph_value},
+                "latency_ms": {"add16_batch256_p50": pct(step_ms, 50),
+                               "add16_batch256_p99": pct(step_ms, 99),
+                               "mul16_batch64_p50": pct(mul_ms, 50),
+                               "mul16_batch64_p99": pct(mul_ms, 99),
+                               "mul16_bootstraps": mul_boots},
                 "e2e": {"value": e2e_val, "unit": UNIT,
-                        "h2d_bytes_per_step": int(n * (2 * 501 * 4 + 1)),
-                        "d2h_bytes_per_step": int(n * 501 * 4)},
-                "gpu_launches": launches0, "roofline": roof, "clocks": clk.summary(),
+                        "h2d_bytes_per_step": int(host_in.nbytes),
+                        "d2h_bytes_per_step": int(n * 16 * 501 * 4)},
+                "gpu_launches": launches, "roofline": roof, "clocks": clk.summary(),
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     ctx.close()

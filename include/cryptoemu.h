@@ -205,6 +205,56 @@ ce_status ce_unit_info(int unit, int cond, int width, int *n_inputs, int *n_outp
  * buf NULL only *used is set. */
 ce_status ce_unit_netlist(int unit, int cond, int width, int32_t *buf, size_t cap, size_t *used);
 
+/* Evaluates a unit over n independent operand sets on device buffers:
+ * d_in is [n][n_inputs][501] ciphertexts, d_out [n][n_outputs][501].  All
+ * gates of one level of all n sets form one batched launch (linear
+ * combination + modulus switch, blind rotation, extraction + key switch);
+ * the whole unit is planned once per (unit, cond, n, buffers) and replayed
+ * as a captured CUDA graph on `cuda_stream` (asynchronous). */
+ce_status ce_unit_eval_device(ce_ctx *ctx, int client, int unit, int cond,
+                              const uint32_t *d_in, uint32_t *d_out, size_t n,
+                              void *cuda_stream);
+/* Graph replay of ce_unit_eval_device on (1, default) or off (eager). */
+ce_status ce_set_unit_graphs(ce_ctx *ctx, int on);
+
+/* ------------------------------------------- encrypted register programs --- */
+
+/* Instructions over a client's encrypted register file of 8 16-bit
+ * registers and its encrypted NZCV flags (§4 "Data Processing": load-store
+ * machine over vRegs; §6 conditional flags).  The program counter and the
+ * instructions are cleartext; registers and flags stay encrypted. */
+typedef enum {
+    CE_I_ADD = 0,      /* rd = rn + rm (parallel-prefix adder) */
+    CE_I_SUB = 1,      /* rd = rn - rm */
+    CE_I_AND = 2,      /* rd = rn & rm */
+    CE_I_ORR = 3,      /* rd = rn | rm */
+    CE_I_LSL = 4,      /* rd = rn << (rm mod 16) (barrel shifter) */
+    CE_I_LSL_IMM = 5,  /* rd = rn << (imm mod 16) (no bootstrap) */
+    CE_I_MUL = 6,      /* rd = (rn * rm) mod 2^16 */
+    CE_I_UDIV = 7,     /* rd = rn / rm, 0 when rm = 0 */
+    CE_I_CMP = 8,      /* NZCV = flags(rn - rm) */
+    CE_I_CSEL = 9,     /* rd = cond(NZCV) ? rn : rm (cond as for CE_U_CSEL) */
+    CE_I_MOV = 10,     /* rd = rn (no bootstrap) */
+    CE_I_MOV_IMM = 11  /* rd = imm (8-bit, zero extended; trivial ciphertexts) */
+} ce_opcode;
+typedef struct { uint8_t op, rd, rn, rm, imm, cond; } ce_insn;
+
+/* Register file access with host ciphertexts (bit 0 first; blocking).
+ * Registers not written hold trivial encryptions of 0. */
+ce_status ce_reg_write(ce_ctx *ctx, int client, int reg, const ce_lwe bits[16]);
+ce_status ce_reg_read(ce_ctx *ctx, int client, int reg, ce_lwe bits[16]);
+ce_status ce_flags_read(ce_ctx *ctx, int client, ce_lwe nzcv[4]);
+/* Runs a program to completion on the client's registers (blocking on the
+ * host until every instruction is enqueued; results are read with
+ * ce_reg_read).  Malformed instructions give CE_EINVAL; timeout_ns > 0
+ * bounds the host time (CE_ETIMEOUT). */
+ce_status ce_exec(ce_ctx *ctx, int client, const ce_insn *prog, size_t n, uint64_t timeout_ns);
+/* Runs several programs concurrently: their instructions advance level by
+ * level together, so gates of different programs and clients share each
+ * batched launch. */
+ce_status ce_exec_multi(ce_ctx *ctx, size_t n_programs, const int *clients,
+                        const ce_insn *const *progs, const size_t *lens, uint64_t timeout_ns);
+
 /* The paper has no counterpart to this call.  Same as ce_gates_batch_device
  * (same kernels, same results) but it allocates no device memory: for
  * callers that cannot let the library call cudaMalloc, e.g. a serving loop

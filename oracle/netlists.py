@@ -309,7 +309,10 @@ def eval_ciphertext(keys, net: Net, inputs):
                            [rd(t[2]) for t in plain])
             for t, o in zip(plain, outs):
                 val[t[4]] = o
-        for t in lvl:
-            if t[0] == MUX:
-                val[t[4]] = O.mux(keys, rd(t[1]), rd(t[2]), rd(t[3]))
+        muxes = [t for t in lvl if t[0] == MUX]
+        if muxes:
+            outs = O.muxes(keys, [rd(t[1]) for t in muxes], [rd(t[2]) for t in muxes],
+                           [rd(t[3]) for t in muxes])
+            for t, o in zip(muxes, outs):
+                val[t[4]] = o
     return [rd(r) for r in net.outputs]

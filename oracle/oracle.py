@@ -124,6 +124,8 @@ def lib():
         L.or_not.argtypes = [P, u32p, u32p]
         L.or_gates_threaded.argtypes = [P, u32p, u32p, u32p, u32p, u32p, u32p,
                                         ctypes.c_int64, ctypes.c_int32]
+        L.or_muxes_threaded.argtypes = [P, u32p, u32p, u32p, u32p, u32p, u32p,
+                                        ctypes.c_int64, ctypes.c_int32]
         _lib = L
     return _lib
 
@@ -266,6 +268,19 @@ def gates(keys: Keys, ops, c1, c2, threads: int | None = None) -> np.ndarray:
     thr = threads or os.cpu_count() or 1
     lib().or_gates_threaded(ctypes.byref(p.c()), _ptr(keys.bsk), _ptr(keys.ksk), _ptr(ops),
                             _ptr(c1), _ptr(c2), _ptr(out), len(ops), thr)
+    return out
+
+
+def muxes(keys: Keys, a, b, c, threads: int | None = None) -> np.ndarray:
+    """Many independent MUX gates (a ? b : c), spread over POSIX threads."""
+    p = keys.params
+    a = _u32(a).reshape(-1, p.n + 1)
+    b = _u32(b).reshape(-1, p.n + 1)
+    c = _u32(c).reshape(-1, p.n + 1)
+    out = np.zeros_like(a)
+    thr = threads or os.cpu_count() or 1
+    lib().or_muxes_threaded(ctypes.byref(p.c()), _ptr(keys.bsk), _ptr(keys.ksk), _ptr(a), _ptr(b),
+                            _ptr(c), _ptr(out), len(a), thr)
     return out
 
 

@@ -423,3 +423,38 @@ void or_gates_threaded(const or_params *p, const uint32_t *bsk, const uint32_t *
     for (int32_t i = 0; i < threads; i++) pthread_join(th[i], 0);
     free(th);
 }
+
+/* Runs `count` independent MUX gates on `threads` POSIX threads (same plain
+ * or_mux; threading only spreads independent gates over cores). */
+typedef struct {
+    const or_params *p; const uint32_t *bsk, *ksk;
+    const uint32_t *a, *b, *c; uint32_t *out; int64_t count; int64_t next;
+    pthread_mutex_t lock;
+} mux_job;
+
+static void *mux_worker(void *arg)
+{
+    mux_job *jb = (mux_job *)arg;
+    const int64_t w = jb->p->n + 1;
+    for (;;) {
+        pthread_mutex_lock(&jb->lock);
+        int64_t g = jb->next++;
+        pthread_mutex_unlock(&jb->lock);
+        if (g >= jb->count) break;
+        or_mux(jb->p, jb->bsk, jb->ksk, jb->a + g * w, jb->b + g * w, jb->c + g * w,
+               jb->out + g * w);
+    }
+    return 0;
+}
+
+void or_muxes_threaded(const or_params *p, const uint32_t *bsk, const uint32_t *ksk,
+                       const uint32_t *a, const uint32_t *b, const uint32_t *c,
+                       uint32_t *out, int64_t count, int32_t threads)
+{
+    mux_job jb = { p, bsk, ksk, a, b, c, out, count, 0, PTHREAD_MUTEX_INITIALIZER };
+    if (threads < 1) threads = 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)threads);
+    for (int32_t i = 0; i < threads; i++) pthread_create(&th[i], 0, mux_worker, &jb);
+    for (int32_t i = 0; i < threads; i++) pthread_join(th[i], 0);
+    free(th);
+}

@@ -88,6 +88,9 @@ void or_gates_threaded(const or_params *p, const uint32_t *bsk, const uint32_t *
                        const int32_t *ops, const uint32_t *c1, const uint32_t *c2,
                        uint32_t *out, int64_t count, int32_t threads);
 void or_not(const or_params *p, const uint32_t *c, uint32_t *out);
+void or_muxes_threaded(const or_params *p, const uint32_t *bsk, const uint32_t *ksk,
+                       const uint32_t *a, const uint32_t *b, const uint32_t *c,
+                       uint32_t *out, int64_t count, int32_t threads);
 
 #ifdef __cplusplus
 }

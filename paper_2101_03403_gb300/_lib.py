@@ -72,6 +72,13 @@ def lib() -> ctypes.CDLL:
         "ce_unit_info": (i32, [i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "ce_unit_netlist": (i32, [i32, i32, i32, vp, sz, ctypes.POINTER(sz)]),
+        "ce_unit_eval_device": (i32, [vp, i32, i32, i32, vp, vp, sz, vp]),
+        "ce_set_unit_graphs": (i32, [vp, i32]),
+        "ce_reg_write": (i32, [vp, i32, i32, vp]),
+        "ce_reg_read": (i32, [vp, i32, i32, vp]),
+        "ce_flags_read": (i32, [vp, i32, vp]),
+        "ce_exec": (i32, [vp, i32, vp, sz, u64]),
+        "ce_exec_multi": (i32, [vp, sz, vp, vp, vp, u64]),
         "ce_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), i32]),
     }
     for name, (res, args) in sig.items():
@@ -343,3 +350,65 @@ def ce_unit_netlist(unit, cond: int = 0, width: int = 16) -> dict:
     o = buf[5 + 9 * n_g:].reshape(n_o, 2)
     return {"n_inputs": n_in, "n_wires": n_wires, "depth": depth, "gates": gates,
             "outputs": [(int(x), bool(y)) for x, y in o]}
+
+
+OPCODES = ["ADD", "SUB", "AND", "ORR", "LSL", "LSL_IMM", "MUL", "UDIV", "CMP", "CSEL", "MOV",
+           "MOV_IMM"]
+OPCODE_ID = {o: i for i, o in enumerate(OPCODES)}
+CONDS = ["EQ", "NE", "CS", "CC", "MI", "PL", "VS", "VC", "HI", "LS", "GE", "LT", "GT", "LE"]
+
+
+class Insn(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_uint8), ("rd", ctypes.c_uint8), ("rn", ctypes.c_uint8),
+                ("rm", ctypes.c_uint8), ("imm", ctypes.c_uint8), ("cond", ctypes.c_uint8)]
+
+
+def insn(op, rd=0, rn=0, rm=0, imm=0, cond=0) -> Insn:
+    op = OPCODE_ID[op] if isinstance(op, str) else int(op)
+    cond = CONDS.index(cond) if isinstance(cond, str) else int(cond)
+    return Insn(op, rd, rn, rm, imm, cond)
+
+
+def ce_unit_eval_device(ctx: Context, client: int, unit, d_in, d_out, n: int, cond: int = 0,
+                        stream=None):
+    _check(lib().ce_unit_eval_device(ctx.ptr, client, _unit(unit), cond, _addr(d_in), _addr(d_out),
+                                     n, _stream(stream)), "ce_unit_eval_device")
+
+
+def ce_set_unit_graphs(ctx: Context, on: bool):
+    _check(lib().ce_set_unit_graphs(ctx.ptr, int(on)), "ce_set_unit_graphs")
+
+
+def ce_reg_write(ctx: Context, client: int, reg: int, bits):
+    bits = _host(bits).reshape(16, LWE_WORDS)
+    _check(lib().ce_reg_write(ctx.ptr, client, reg, bits.ctypes.data), "ce_reg_write")
+
+
+def ce_reg_read(ctx: Context, client: int, reg: int) -> np.ndarray:
+    out = np.zeros((16, LWE_WORDS), np.uint32)
+    _check(lib().ce_reg_read(ctx.ptr, client, reg, out.ctypes.data), "ce_reg_read")
+    return out
+
+
+def ce_flags_read(ctx: Context, client: int) -> np.ndarray:
+    out = np.zeros((4, LWE_WORDS), np.uint32)
+    _check(lib().ce_flags_read(ctx.ptr, client, out.ctypes.data), "ce_flags_read")
+    return out
+
+
+def _prog(prog):
+    arr = (Insn * max(len(prog), 1))(*prog)
+    return arr, len(prog)
+
+
+def ce_exec(ctx: Context, client: int, prog, timeout_ns: int = 0):
+    arr, n = _prog(prog)
+    _check(lib().ce_exec(ctx.ptr, client, ctypes.addressof(arr), n, timeout_ns), "ce_exec")
+
+
+def ce_exec_multi(ctx: Context, clients, progs, timeout_ns: int = 0):
+    arrs = [_prog(p) for p in progs]
+    cl = (ctypes.c_int * len(clients))(*clients)
+    ptrs = (ctypes.c_void_p * len(progs))(*[ctypes.addressof(a) for a, _ in arrs])
+    lens = (ctypes.c_size_t * len(progs))(*[n for _, n in arrs])
+    _check(lib().ce_exec_multi(ctx.ptr, len(progs), cl, ptrs, lens, timeout_ns), "ce_exec_multi")

@@ -64,47 +64,15 @@ void transform_tables(uint64_t *out) {
 
 using namespace ce;
 
+#include "ctx.h"
+
 namespace {
-
-constexpr uint64_t kBskNttBytes = kBskNttWords * 8;
-constexpr uint64_t kKskDevBytes = kKskDevWords * 4;
-constexpr uint64_t kClientBytes = kBskNttBytes + kKskDevBytes;
-
-struct Client {
-  bool live = false;
-  uint64_t *bsk = nullptr;  // transform-domain bootstrapping key
-  uint32_t *ksk = nullptr;  // [j][q][v-1][512]
-};
 
 ce_status cuda_fail(cudaError_t e, const char *where) {
   return set_error(CE_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
 }  // namespace
-
-struct ce_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  int sms = 0;
-  uint64_t budget = 0, used = 0;
-  std::vector<Client> clients;
-  uint64_t *tw = nullptr;
-  int *err = nullptr;
-  uint16_t *abar = nullptr;
-  uint32_t *acc = nullptr;
-  size_t job_cap = 0;
-  uint8_t *io_ops = nullptr;
-  uint32_t *io_a = nullptr, *io_b = nullptr, *io_out = nullptr;
-  size_t io_cap = 0;
-  int cfg_g = 0, cfg_bps = 0;
-  int last_launches = 0;
-  // Optional per-kernel timing: event pairs recorded around each launch on
-  // the launching stream, summed by ce_profile_read.
-  bool profile = false;
-  std::vector<cudaEvent_t> ev_pool;
-  struct Timed { int kind; cudaEvent_t a, b; };
-  std::vector<Timed> timed;
-};
 
 namespace {
 
@@ -176,29 +144,6 @@ void ks_config(const ce_ctx *ctx, size_t n_out, int *tile, int *jsplit) {
   *jsplit = int(js);
 }
 
-cudaEvent_t take_event(ce_ctx *ctx) {
-  if (!ctx->ev_pool.empty()) {
-    cudaEvent_t e = ctx->ev_pool.back();
-    ctx->ev_pool.pop_back();
-    return e;
-  }
-  cudaEvent_t e = nullptr;
-  cudaEventCreate(&e);
-  return e;
-}
-
-// Records an event pair around `launch` when profiling is on.
-template <class F>
-cudaError_t timed_launch(ce_ctx *ctx, int kind, cudaStream_t st, F launch) {
-  if (!ctx->profile) return launch();
-  cudaEvent_t a = take_event(ctx), b = take_event(ctx);
-  cudaEventRecord(a, st);
-  cudaError_t e = launch();
-  cudaEventRecord(b, st);
-  ctx->timed.push_back({kind, a, b});
-  return e;
-}
-
 // Jobs -> blind rotation -> extraction/key switching on device buffers.
 ce_status run_path(ce_ctx *ctx, Client *cl, int mode, const uint8_t *ops, const uint32_t *a,
                    const uint32_t *b, const uint32_t *c, uint32_t *out, size_t n,
@@ -212,14 +157,14 @@ ce_status run_path(ce_ctx *ctx, Client *cl, int mode, const uint8_t *ops, const 
   ce_status s = ensure_jobs(ctx, jobs);
   if (s != CE_OK) return s;
   int launches = 0;
-  cudaError_t e = timed_launch(ctx, 0, st, [&] {
+  cudaError_t e = ce::timed(ctx, 0, st, [&] {
     return launch_lincomb_modswitch(ops, a, b, c, ctx->abar, int(jobs), mode, ctx->err, st);
   });
   if (e != cudaSuccess) return cuda_fail(e, "lincomb_modswitch");
   ++launches;
   int G, blocks;
   br_config(ctx, jobs, &G, &blocks);
-  e = timed_launch(ctx, 1, st, [&] {
+  e = ce::timed(ctx, 1, st, [&] {
     return launch_blind_rotate(cl->bsk, ctx->abar, ctx->acc, int(jobs), ctx->tw, ctx->err, G,
                                blocks, st);
   });
@@ -231,7 +176,7 @@ ce_status run_path(ce_ctx *ctx, Client *cl, int mode, const uint8_t *ops, const 
     e = cudaMemsetAsync(out, 0, n * kLweWords * sizeof(uint32_t), st);
     if (e != cudaSuccess) return cuda_fail(e, "memset");
   }
-  e = timed_launch(ctx, 2, st, [&] {
+  e = ce::timed(ctx, 2, st, [&] {
     return launch_extract_keyswitch(ctx->acc, cl->ksk, out, int(n), mode != 0, tile, jsplit, st);
   });
   if (e != cudaSuccess) return cuda_fail(e, "extract_keyswitch");
@@ -307,6 +252,8 @@ extern "C" void ce_destroy(ce_ctx *ctx) {
   cudaFree(ctx->io_a);
   cudaFree(ctx->io_b);
   cudaFree(ctx->io_out);
+  engine_destroy(ctx->engine);
+  ctx->engine = nullptr;
   for (auto &t : ctx->timed) {
     cudaEventDestroy(t.a);
     cudaEventDestroy(t.b);
@@ -383,6 +330,7 @@ extern "C" ce_status ce_client_evict(ce_ctx *ctx, int client_id) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
+  engine_drop_client(ctx->engine, client_id);
   cudaFree(cl->bsk);
   cudaFree(cl->ksk);
   *cl = Client();
@@ -533,6 +481,27 @@ void gate_path_shape(const ce_ctx *ctx, size_t jobs, size_t n_out, int *G, int *
                      int *tile, int *jsplit) {
   br_config(ctx, jobs, G, blocks);
   ks_config(ctx, n_out, tile, jsplit);
+}
+
+}  // namespace ce
+
+namespace ce {
+
+ce_status cuda_error(cudaError_t e, const char *where) { return cuda_fail(e, where); }
+ce_status ensure_job_scratch(ce_ctx *ctx, size_t jobs) { return ensure_jobs(ctx, jobs); }
+void br_shape(const ce_ctx *ctx, size_t jobs, int *G, int *blocks) { br_config(ctx, jobs, G, blocks); }
+void ks_shape(const ce_ctx *ctx, size_t n_out, int *tile, int *jsplit) {
+  ks_config(ctx, n_out, tile, jsplit);
+}
+cudaEvent_t take_event(ce_ctx *ctx) {
+  if (!ctx->ev_pool.empty()) {
+    cudaEvent_t e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
 }
 
 }  // namespace ce

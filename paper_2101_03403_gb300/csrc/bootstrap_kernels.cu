@@ -65,6 +65,32 @@ __global__ void __launch_bounds__(512) lincomb_modswitch_kernel(
   }
 }
 
+// Gather variant for the netlist engine: job j reads its two inputs from
+// arena slots (kSlotWords words each), with optional negation (NOT is free:
+// it flips the sign of the input's weight).  op 10/11 are the two halves of
+// a MUX (AND-part with (s, x), ANDNY-part with (s, y)).
+__global__ void __launch_bounds__(512) lincomb_gather_kernel(const GateJob *__restrict__ jobs,
+                                                             const uint32_t *__restrict__ arena,
+                                                             uint16_t *__restrict__ abar,
+                                                             int *__restrict__ err) {
+  const int job = blockIdx.x;
+  const GateJob J = jobs[job];
+  int op = J.op;
+  if (op > 11) {
+    if (threadIdx.x == 0) atomicExch(err, 2);
+    op = 0;
+  }
+  const int m = threadIdx.x;
+  if (m < kLweWords) {
+    const uint32_t w1 = uint32_t(int32_t(c_s1[op]) * (J.neg_a ? -1 : 1));
+    const uint32_t w2 = uint32_t(int32_t(c_s2[op]) * (J.neg_b ? -1 : 1));
+    const uint32_t x = w1 * arena[size_t(J.a) * kSlotWords + m] +
+                       w2 * arena[size_t(J.b) * kSlotWords + m] +
+                       (m == kLweN ? uint32_t(int32_t(c_kappa8[op])) * kMuEighth : 0u);
+    abar[size_t(job) * kAbarStride + m] = uint16_t(((x + (1u << 20)) >> 21) & 2047u);
+  }
+}
+
 // ------------------------------------------------------------------- K2 ---
 // Persistent batched blind rotation.  A block holds G gates (128 threads
 // each) and streams the bootstrapping key once per block: the transform-
@@ -142,9 +168,9 @@ struct BrSmem {
 
 template <int G, int NSLOT>
 __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
-    const uint64_t *__restrict__ bsk, const uint16_t *__restrict__ abar,
-    uint32_t *__restrict__ acc_out, int n_jobs, const uint64_t *__restrict__ tw,
-    int *__restrict__ err) {
+    const uint64_t *__restrict__ bsk, const uint64_t *const *__restrict__ grp_bsk,
+    const uint16_t *__restrict__ abar, uint32_t *__restrict__ acc_out, int n_jobs,
+    const uint64_t *__restrict__ tw, int *__restrict__ err) {
   using L = BrSmem<G, NSLOT>;
   extern __shared__ __align__(128) uint8_t smem[];
   uint64_t *ring = reinterpret_cast<uint64_t *>(smem);
@@ -173,10 +199,16 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  // Key of the gate group that consumes chunk c of this block (one key per
+  // group; all gates of a group belong to the same client).
+  auto chunk_src = [&](int c) {
+    const uint64_t *key = bsk;
+    if (grp_bsk) key = grp_bsk[blockIdx.x + (c / kChunksPerGate) * gridDim.x];
+    return key + size_t(c % kChunksPerGate) * kChunkWords;
+  };
   if (threadIdx.x == 0) {
     for (int c = 0; c < NSLOT && c < total_chunks; ++c)
-      issue_chunk(ring + size_t(c) * kChunkWords, smem_u32(full + c),
-                  bsk + size_t(c % kChunksPerGate) * kChunkWords);
+      issue_chunk(ring + size_t(c) * kChunkWords, smem_u32(full + c), chunk_src(c));
   }
 
   const int P = t >> 6, n1 = t & 63;
@@ -256,7 +288,7 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
             const int next = chunk + NSLOT;
             if (next < total_chunks && !*abort)
               issue_chunk(ring + size_t(slot) * kChunkWords, smem_u32(full + slot),
-                          bsk + size_t(next % kChunksPerGate) * kChunkWords);
+                          chunk_src(next));
           }
         }
       }
@@ -281,26 +313,39 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
 // Fused sample extraction (coefficient 0: a'_0 = A_0, a'_j = -A_{N-j},
 // b' = B_0) and key switching: each a'_j rounded to 16 bits, split into 8
 // base-4 digits (most significant first), out = (0, b') - sum KSK[j][q][digit].
-// A block serves GT jobs for a range of j; the three KSK rows of (j, q) are
-// read once (uint4 per thread) and applied to all GT jobs.  With several
-// j-ranges the partial sums are added atomically (exact mod 2^32).  In MUX
-// mode an output combines jobs 2i and 2i+1 plus (0, +1/8) before switching.
-template <int GT, bool MUX>
+// A block serves GT outputs for a range of j; the three KSK rows of (j, q) are
+// read once (uint4 per thread) and applied to all GT outputs.  With several
+// j-ranges the partial sums are added atomically (exact mod 2^32; the
+// outputs start at zero).  An output combines one accumulator, or two plus
+// (0, +1/8) for a MUX, before switching.  MODE 0: output o = job o, packed
+// [n][501] output; MODE 1: MUX, jobs 2o and 2o+1, packed output; MODE 2:
+// descriptors (jobs, arena slot) from `outs`, written to the arena.  With
+// tile_ksk set, tile t uses the key tile_ksk[t] (one client per tile).
+template <int GT, int MODE>
 __global__ void __launch_bounds__(128) extract_keyswitch_kernel(
-    const uint32_t *__restrict__ acc, const uint32_t *__restrict__ ksk,
+    const uint32_t *__restrict__ acc, const uint32_t *__restrict__ ksk_one,
+    const uint32_t *const *__restrict__ tile_ksk, const GateOut *__restrict__ outs,
     uint32_t *__restrict__ out, int n_out, int jchunk) {
   extern __shared__ uint16_t hbits[];  // [GT][jchunk]
   const int tile = blockIdx.x, j0 = blockIdx.y * jchunk;
   const int j1 = min(kRingN, j0 + jchunk);
+  const uint32_t *ksk = tile_ksk ? tile_ksk[tile] : ksk_one;
+  auto jobs_of = [&](int o, int &j1x, int &j2x) {
+    if (MODE == 0) { j1x = o; j2x = -1; }
+    else if (MODE == 1) { j1x = 2 * o; j2x = 2 * o + 1; }
+    else { j1x = outs[o].job1; j2x = outs[o].job2; }
+  };
   for (int idx = threadIdx.x; idx < GT * jchunk; idx += 128) {
     const int g = idx / jchunk, j = j0 + idx % jchunk;
     const int o = tile * GT + g;
     uint32_t h = 0;
     if (o < n_out && j < j1) {
-      const uint32_t *A = acc + size_t(MUX ? 2 * o : o) * 2 * kRingN;
+      int ja, jb;
+      jobs_of(o, ja, jb);
+      const uint32_t *A = acc + size_t(ja) * 2 * kRingN;
       uint32_t aj = (j == 0) ? A[0] : 0u - A[kRingN - j];
-      if (MUX) {
-        const uint32_t *A2 = A + 2 * kRingN;
+      if (jb >= 0) {
+        const uint32_t *A2 = acc + size_t(jb) * 2 * kRingN;
         aj += (j == 0) ? A2[0] : 0u - A2[kRingN - j];
       }
       h = (aj + 0x8000u) >> 16;
@@ -340,23 +385,32 @@ __global__ void __launch_bounds__(128) extract_keyswitch_kernel(
   for (int g = 0; g < GT; ++g) {
     const int o = tile * GT + g;
     if (o >= n_out) break;
-    const uint32_t *A = acc + size_t(MUX ? 2 * o : o) * 2 * kRingN;
+    int ja, jb;
+    jobs_of(o, ja, jb);
+    uint32_t *dst = MODE == 2 ? out + size_t(outs[o].slot) * kSlotWords : out + size_t(o) * kLweWords;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int m = 4 * threadIdx.x + e;
       if (m >= kLweWords) continue;
       uint32_t val = 0u - s[g][e];
       if (m == kLweN && blockIdx.y == 0) {
-        uint32_t bp = A[kRingN];
-        if (MUX) bp += A[2 * kRingN + kRingN] + kMuEighth;
+        uint32_t bp = acc[size_t(ja) * 2 * kRingN + kRingN];
+        if (jb >= 0) bp += acc[size_t(jb) * 2 * kRingN + kRingN] + kMuEighth;
         val += bp;
       }
       if (gridDim.y == 1)
-        out[size_t(o) * kLweWords + m] = val;
+        dst[m] = val;
       else
-        atomicAdd(out + size_t(o) * kLweWords + m, val);
+        atomicAdd(dst + m, val);
     }
   }
+}
+
+// Zeroes the output words of descriptor-addressed outputs (before a split
+// key switch accumulates into them atomically).
+__global__ void zero_slots_kernel(const GateOut *__restrict__ outs, uint32_t *__restrict__ arena) {
+  const uint32_t slot = outs[blockIdx.x].slot;
+  for (int m = threadIdx.x; m < kLweWords; m += blockDim.x) arena[size_t(slot) * kSlotWords + m] = 0;
 }
 
 // --------------------------------------------------------- key to transform ---
@@ -413,14 +467,15 @@ __global__ void __launch_bounds__(128) negacyclic_mul_kernel(const int16_t *__re
 }
 
 template <int G, int NSLOT>
-cudaError_t launch_br(const uint64_t *bsk, const uint16_t *abar, uint32_t *acc, int n,
-                      const uint64_t *tw, int *err, int blocks, cudaStream_t st) {
+cudaError_t launch_br(const uint64_t *bsk, const uint64_t *const *grp_bsk, const uint16_t *abar,
+                      uint32_t *acc, int n, const uint64_t *tw, int *err, int blocks,
+                      cudaStream_t st) {
   using L = BrSmem<G, NSLOT>;
   auto kern = blind_rotate_kernel<G, NSLOT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(L::kTotal));
   if (e != cudaSuccess) return e;
-  kern<<<blocks, 128 * G, L::kTotal, st>>>(bsk, abar, acc, n, tw, err);
+  kern<<<blocks, 128 * G, L::kTotal, st>>>(bsk, grp_bsk, abar, acc, n, tw, err);
   return cudaGetLastError();
 }
 
@@ -444,31 +499,57 @@ cudaError_t launch_lincomb_modswitch(const uint8_t *ops, const uint32_t *a, cons
 
 cudaError_t launch_blind_rotate(const uint64_t *bsk, const uint16_t *abar, uint32_t *acc,
                                 int n_jobs, const uint64_t *tw, int *err, int gates_per_block,
-                                int blocks, cudaStream_t st) {
+                                int blocks, cudaStream_t st, const uint64_t *const *grp_bsk) {
   if (n_jobs <= 0) return cudaSuccess;
   switch (gates_per_block) {
-    case 1: return launch_br<1, 2>(bsk, abar, acc, n_jobs, tw, err, blocks, st);
-    case 2: return launch_br<2, 3>(bsk, abar, acc, n_jobs, tw, err, blocks, st);
-    default: return launch_br<4, 3>(bsk, abar, acc, n_jobs, tw, err, blocks, st);
+    case 1: return launch_br<1, 2>(bsk, grp_bsk, abar, acc, n_jobs, tw, err, blocks, st);
+    case 2: return launch_br<2, 3>(bsk, grp_bsk, abar, acc, n_jobs, tw, err, blocks, st);
+    default: return launch_br<4, 3>(bsk, grp_bsk, abar, acc, n_jobs, tw, err, blocks, st);
   }
+}
+
+template <int GT>
+void launch_ks_tile(int mode, dim3 grid, size_t sm, cudaStream_t st, const uint32_t *acc,
+                    const uint32_t *ksk, const uint32_t *const *tile_ksk, const GateOut *outs,
+                    uint32_t *out, int n_out, int jchunk) {
+  if (mode == 0)
+    extract_keyswitch_kernel<GT, 0><<<grid, 128, sm, st>>>(acc, ksk, tile_ksk, outs, out, n_out, jchunk);
+  else if (mode == 1)
+    extract_keyswitch_kernel<GT, 1><<<grid, 128, sm, st>>>(acc, ksk, tile_ksk, outs, out, n_out, jchunk);
+  else
+    extract_keyswitch_kernel<GT, 2><<<grid, 128, sm, st>>>(acc, ksk, tile_ksk, outs, out, n_out, jchunk);
 }
 
 cudaError_t launch_extract_keyswitch(const uint32_t *acc, const uint32_t *ksk, uint32_t *out,
                                      int n_out, bool mux, int tile, int jsplit, cudaStream_t st) {
+  return launch_extract_keyswitch_ex(acc, ksk, nullptr, nullptr, out, n_out, mux ? 1 : 0, tile,
+                                     jsplit, st);
+}
+
+cudaError_t launch_extract_keyswitch_ex(const uint32_t *acc, const uint32_t *ksk,
+                                        const uint32_t *const *tile_ksk, const GateOut *outs,
+                                        uint32_t *out, int n_out, int mode, int tile, int jsplit,
+                                        cudaStream_t st) {
   if (n_out <= 0) return cudaSuccess;
   const int jchunk = (kRingN + jsplit - 1) / jsplit;
   const dim3 grid((n_out + tile - 1) / tile, jsplit);
   const size_t sm = size_t(tile) * jchunk * sizeof(uint16_t);
-  if (tile == 1) {
-    if (mux) extract_keyswitch_kernel<1, true><<<grid, 128, sm, st>>>(acc, ksk, out, n_out, jchunk);
-    else extract_keyswitch_kernel<1, false><<<grid, 128, sm, st>>>(acc, ksk, out, n_out, jchunk);
-  } else if (tile == 4) {
-    if (mux) extract_keyswitch_kernel<4, true><<<grid, 128, sm, st>>>(acc, ksk, out, n_out, jchunk);
-    else extract_keyswitch_kernel<4, false><<<grid, 128, sm, st>>>(acc, ksk, out, n_out, jchunk);
-  } else {
-    if (mux) extract_keyswitch_kernel<16, true><<<grid, 128, sm, st>>>(acc, ksk, out, n_out, jchunk);
-    else extract_keyswitch_kernel<16, false><<<grid, 128, sm, st>>>(acc, ksk, out, n_out, jchunk);
-  }
+  if (tile == 1) launch_ks_tile<1>(mode, grid, sm, st, acc, ksk, tile_ksk, outs, out, n_out, jchunk);
+  else if (tile == 4) launch_ks_tile<4>(mode, grid, sm, st, acc, ksk, tile_ksk, outs, out, n_out, jchunk);
+  else launch_ks_tile<16>(mode, grid, sm, st, acc, ksk, tile_ksk, outs, out, n_out, jchunk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lincomb_gather(const GateJob *jobs, const uint32_t *arena, uint16_t *abar,
+                                  int n_jobs, int *err, cudaStream_t st) {
+  if (n_jobs <= 0) return cudaSuccess;
+  lincomb_gather_kernel<<<n_jobs, 512, 0, st>>>(jobs, arena, abar, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_slots(const GateOut *outs, uint32_t *arena, int n_out, cudaStream_t st) {
+  if (n_out <= 0) return cudaSuccess;
+  zero_slots_kernel<<<n_out, 128, 0, st>>>(outs, arena);
   return cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@ constexpr uint32_t kMuEighth = 0x20000000u;   // +1/8
 // Device layouts.
 constexpr int kAbarStride = 512;      // uint16 words per gate: abar[500], bbar, pad
 constexpr int kKskRow = 512;          // padded KSK row: a[500], b, 11 zero words
+constexpr int kSlotWords = 512;       // engine arena slot: a[500], b, padding
 // Key-switching key on the device keeps only v = 1..3 (v = 0 adds nothing):
 // [j][q][v-1][kKskRow] uint32.
 constexpr uint64_t kKskDevWords = uint64_t(kRingN) * kKsT * 3 * kKskRow;

@@ -1,0 +1,75 @@
+// The context object behind the C ABI (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "ce_internal.h"
+
+namespace ce {
+
+constexpr uint64_t kBskNttBytes = kBskNttWords * 8;
+constexpr uint64_t kKskDevBytes = kKskDevWords * 4;
+constexpr uint64_t kClientBytes = kBskNttBytes + kKskDevBytes;
+
+struct Client {
+  bool live = false;
+  uint64_t *bsk = nullptr;  // transform-domain bootstrapping key
+  uint32_t *ksk = nullptr;  // [j][q][v-1][512]
+};
+
+class Engine;  // netlist engine (engine.cu), created on first use
+
+}  // namespace ce
+
+struct ce_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sms = 0;
+  uint64_t budget = 0, used = 0;
+  std::vector<ce::Client> clients;
+  uint64_t *tw = nullptr;
+  int *err = nullptr;
+  uint16_t *abar = nullptr;
+  uint32_t *acc = nullptr;
+  size_t job_cap = 0;
+  uint8_t *io_ops = nullptr;
+  uint32_t *io_a = nullptr, *io_b = nullptr, *io_out = nullptr;
+  size_t io_cap = 0;
+  int cfg_g = 0, cfg_bps = 0;
+  int last_launches = 0;
+  // Optional per-kernel timing: event pairs recorded around each launch on
+  // the launching stream, summed by ce_profile_read.
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Timed { int kind; cudaEvent_t a, b; };
+  std::vector<Timed> timed;
+  ce::Engine *engine = nullptr;
+};
+
+namespace ce {
+
+// Shared helpers of the context translation units.
+ce_status cuda_error(cudaError_t e, const char *where);
+ce_status ensure_job_scratch(ce_ctx *ctx, size_t jobs);
+cudaEvent_t take_event(ce_ctx *ctx);
+void br_shape(const ce_ctx *ctx, size_t jobs, int *G, int *blocks);
+void ks_shape(const ce_ctx *ctx, size_t n_out, int *tile, int *jsplit);
+void engine_destroy(Engine *e);
+void engine_drop_client(Engine *e, int client);
+// Records an event pair around `launch` when profiling is on (kind 0, 1, 2).
+template <class F>
+cudaError_t timed(ce_ctx *ctx, int kind, cudaStream_t st, F launch) {
+  if (!ctx->profile) return launch();
+  cudaEvent_t a = take_event(ctx), b = take_event(ctx);
+  cudaEventRecord(a, st);
+  cudaError_t e = launch();
+  cudaEventRecord(b, st);
+  ctx->timed.push_back({kind, a, b});
+  return e;
+}
+
+}  // namespace ce

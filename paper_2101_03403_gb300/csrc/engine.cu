@@ -1,0 +1,848 @@
+// Level-synchronous netlist engine: functional units and instruction
+// programs over bootstrapped gates, batched across instructions and clients.
+//
+// The paper's emulator evaluates each functional unit with OpenMP sections,
+// one thread per gate, serialised past its 48 cores (§5).  Here every
+// in-flight unit instance (an instruction of some client) contributes the
+// gates of its next level to one "tick": a single batched launch of the
+// linear-combination, blind-rotation and key-switching kernels over all of
+// them.  Ciphertexts live in an arena of 2 KB slots; a wire is a slot plus a
+// negation flag, so NOT, MOV and shifts by a constant cost nothing (§3: they
+// need no bootstrapping).  Slots are reference counted: register bits,
+// running instances and cached plans hold references.
+//
+// Fixed-shape work (one unit over a batch of n operand sets) is planned once
+// — all descriptors of all levels uploaded, arena slots reserved — and
+// replayed as a captured CUDA graph per (unit, shape).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <list>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "ce_internal.h"
+#include "ctx.h"
+#include "launch.h"
+#include "netlist.h"
+
+namespace ce {
+
+namespace {
+
+constexpr uint32_t kSlotFalse = 0;  // the trivial ciphertext (0, -1/8)
+constexpr uint32_t kSlotSink = 1;   // padding outputs land here
+constexpr int kWidth = 16;          // register width
+constexpr int kRegs = 8;
+
+struct SRef {
+  uint32_t slot = kSlotFalse;
+  bool neg = false;
+};
+
+// Copy [n][n_in][501] packed ciphertexts into consecutive arena slots.
+__global__ void copy_in_kernel(const uint32_t *__restrict__ in, uint32_t *__restrict__ arena,
+                               uint32_t base) {
+  const size_t c = blockIdx.x;
+  for (int m = threadIdx.x; m < kLweWords; m += blockDim.x)
+    arena[(size_t(base) + c) * kSlotWords + m] = in[c * kLweWords + m];
+}
+
+// out[c] = (neg ? -1 : 1) * arena[slot] for the (slot, neg) pairs in map.
+__global__ void copy_out_kernel(const uint32_t *__restrict__ map, const uint32_t *__restrict__ arena,
+                                uint32_t *__restrict__ out) {
+  const size_t c = blockIdx.x;
+  const uint32_t slot = map[2 * c], neg = map[2 * c + 1];
+  for (int m = threadIdx.x; m < kLweWords; m += blockDim.x) {
+    const uint32_t v = arena[size_t(slot) * kSlotWords + m];
+    out[c * kLweWords + m] = neg ? 0u - v : v;
+  }
+}
+
+__global__ void fill_false_kernel(uint32_t *__restrict__ arena) {
+  for (int m = threadIdx.x; m < kSlotWords; m += blockDim.x)
+    arena[m] = (m == kLweN) ? 0u - kMuEighth : 0u;
+}
+
+// Descriptors of one tick (one level of every participating instance).
+struct TickDesc {
+  std::vector<GateJob> jobs;
+  std::vector<GateOut> outs;
+  std::vector<const uint64_t *> grp_bsk;
+  std::vector<const uint32_t *> tile_ksk;
+  int G = 1, blocks = 1, tile = 1, jsplit = 1;
+};
+
+size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+}  // namespace
+
+struct Instance {
+  const Netlist *net = nullptr;
+  int client = 0;
+  std::vector<SRef> wire;   // per netlist wire
+  int level = 0;            // levels completed
+  std::vector<SRef> result; // resolved outputs once complete
+};
+
+struct RegFile {
+  SRef r[kRegs][kWidth];
+  SRef nzcv[4];
+};
+
+struct Plan {
+  int unit = 0, cond = 0, client = 0;
+  size_t n = 0;
+  const uint32_t *d_in = nullptr;
+  uint32_t *d_out = nullptr;
+  uint32_t in_base = 0;
+  std::vector<uint32_t> slots;       // all slots the plan owns
+  uint8_t *d_desc = nullptr;         // descriptors of every level + output map
+  struct Level {
+    size_t jobs_off, outs_off, bsk_off, ksk_off;
+    int n_jobs, n_outs, G, blocks, tile, jsplit;
+  };
+  std::vector<Level> levels;
+  size_t map_off = 0;
+  int n_in = 0, n_out = 0;
+  size_t max_jobs = 0;
+  cudaGraphExec_t exec = nullptr;
+  int graph_launches = 0;
+  uint64_t last_use = 0;
+};
+
+class Engine {
+ public:
+  explicit Engine(ce_ctx *c) : ctx(c) {}
+  ~Engine() {
+    for (auto &p : plans) drop_plan(*p);
+    for (int i = 0; i < 2; ++i) {
+      if (h_desc[i]) cudaFreeHost(h_desc[i]);
+      cudaFree(d_desc[i]);
+      if (desc_ev[i]) cudaEventDestroy(desc_ev[i]);
+    }
+    cudaFree(arena);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
+
+  ce_status init() {
+    ce_status s = reserve(1 << 14);
+    if (s != CE_OK) return s;
+    rc.assign(2, 1);  // FALSE and sink are permanent
+    next_slot = 2;
+    fill_false_kernel<<<1, 512, 0, ctx->stream>>>(arena);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&desc_ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_error(e, "engine init");
+    return CE_OK;
+  }
+
+  // ------------------------------------------------------------ arena ---
+  ce_status reserve(size_t slots) {
+    if (slots <= cap) return CE_OK;
+    size_t ncap = cap ? cap : 1;
+    while (ncap < slots) ncap *= 2;
+    uint32_t *na = nullptr;
+    cudaError_t e = cudaMalloc(&na, ncap * kSlotWords * sizeof(uint32_t));
+    if (e != cudaSuccess) return set_error(CE_ENOMEM, "engine: arena allocation failed");
+    if (arena) {
+      // rare: wait for all work that may touch the old arena, then move it
+      e = cudaDeviceSynchronize();
+      if (e == cudaSuccess)
+        e = cudaMemcpy(na, arena, cap * kSlotWords * sizeof(uint32_t), cudaMemcpyDeviceToDevice);
+      cudaFree(arena);
+      // plans captured the old address
+      for (auto &p : plans) drop_graph(*p);
+    }
+    arena = na;
+    cap = ncap;
+    return e == cudaSuccess ? CE_OK : cuda_error(e, "engine: arena growth");
+  }
+  ce_status alloc(uint32_t *out) {
+    if (!free_.empty()) {
+      *out = free_.back();
+      free_.pop_back();
+      rc[*out] = 1;
+      return CE_OK;
+    }
+    if (next_slot >= cap) {
+      ce_status s = reserve(next_slot + 1);
+      if (s != CE_OK) return s;
+    }
+    *out = next_slot++;
+    if (rc.size() <= *out) rc.resize(*out + 1, 0);
+    rc[*out] = 1;
+    return CE_OK;
+  }
+  void ref(const SRef &r) {
+    if (r.slot > kSlotSink) ++rc[r.slot];
+  }
+  void unref(const SRef &r) {
+    if (r.slot > kSlotSink && --rc[r.slot] == 0) free_.push_back(r.slot);
+  }
+
+  const Netlist *netlist(int unit, int cond) {
+    const int key = unit * 16 + cond;
+    auto it = nets.find(key);
+    if (it != nets.end()) return &it->second;
+    Netlist n;
+    if (!build_unit(unit, kWidth, unit == kUnitCsel ? cond : 0, &n)) return nullptr;
+    return &nets.emplace(key, std::move(n)).first->second;
+  }
+
+  RegFile &regs(int client) {
+    auto it = rf.find(client);
+    if (it == rf.end()) it = rf.emplace(client, RegFile{}).first;
+    return it->second;
+  }
+  void drop_client(int client) {
+    auto it = rf.find(client);
+    if (it == rf.end()) return;
+    for (auto &r : it->second.r)
+      for (auto &b : r) unref(b);
+    for (auto &b : it->second.nzcv) unref(b);
+    rf.erase(it);
+    for (auto pit = plans.begin(); pit != plans.end();) {
+      if ((*pit)->client == client) {
+        drop_plan(**pit);
+        pit = plans.erase(pit);
+      } else {
+        ++pit;
+      }
+    }
+  }
+
+  // ---------------------------------------------------------- instance ---
+  ce_status start(Instance &in, const Netlist *net, int client, const std::vector<SRef> &inputs) {
+    in.net = net;
+    in.client = client;
+    in.level = 0;
+    in.wire.assign(net->n_wires, SRef{});
+    for (int i = 0; i < net->n_inputs; ++i) {
+      in.wire[i] = inputs[i];
+      ref(inputs[i]);
+    }
+    return CE_OK;
+  }
+  SRef resolve(const Instance &in, const Ref &r) const {
+    if (r.wire < 0) return SRef{kSlotFalse, r.neg};
+    const SRef &w = in.wire[r.wire];
+    return SRef{w.slot, w.neg != r.neg};
+  }
+  // Outputs taken (one reference each), then the instance's own released.
+  void complete(Instance &in) {
+    in.result.clear();
+    for (const Ref &r : in.net->outputs) {
+      const SRef s = resolve(in, r);
+      ref(s);
+      in.result.push_back(s);
+    }
+    for (const SRef &w : in.wire) unref(w);
+    in.wire.clear();
+  }
+
+  // Builds the descriptors of the next level of every instance (grouped by
+  // client; groups of G jobs and tiles of `tile` outputs never mix clients).
+  ce_status build_tick(const std::vector<Instance *> &act, TickDesc &t) {
+    std::vector<Instance *> order(act);
+    std::stable_sort(order.begin(), order.end(),
+                     [](const Instance *a, const Instance *b) { return a->client < b->client; });
+    size_t total_jobs = 0, total_outs = 0;
+    for (Instance *in : order) {
+      const Netlist &n = *in->net;
+      for (int g = n.level_begin[in->level]; g < n.level_begin[in->level + 1]; ++g) {
+        total_jobs += n.gates[g].op == kOpMux ? 2 : 1;
+        ++total_outs;
+      }
+    }
+    br_shape(ctx, total_jobs, &t.G, &t.blocks);
+    ks_shape(ctx, total_outs, &t.tile, &t.jsplit);
+    t.jobs.clear();
+    t.outs.clear();
+    t.grp_bsk.clear();
+    t.tile_ksk.clear();
+    size_t i = 0;
+    while (i < order.size()) {
+      const int client = order[i]->client;
+      const Client &cl = ctx->clients[client];
+      const size_t job0 = t.jobs.size(), out0 = t.outs.size();
+      for (; i < order.size() && order[i]->client == client; ++i) {
+        Instance &in = *order[i];
+        const Netlist &n = *in.net;
+        for (int g = n.level_begin[in.level]; g < n.level_begin[in.level + 1]; ++g) {
+          const NGate &x = n.gates[g];
+          uint32_t slot;
+          ce_status s = alloc(&slot);
+          if (s != CE_OK) return s;
+          in.wire[x.out] = SRef{slot, false};
+          const SRef a = resolve(in, x.a), b = resolve(in, x.b);
+          GateOut o{};
+          o.slot = slot;
+          o.job1 = int32_t(t.jobs.size());
+          if (x.op == kOpMux) {
+            const SRef c = resolve(in, x.c);
+            t.jobs.push_back(GateJob{a.slot, b.slot, 10, a.neg, b.neg, 0});
+            t.jobs.push_back(GateJob{a.slot, c.slot, 11, a.neg, c.neg, 0});
+            o.job2 = o.job1 + 1;
+          } else {
+            t.jobs.push_back(GateJob{a.slot, b.slot, x.op, a.neg, b.neg, 0});
+            o.job2 = -1;
+          }
+          t.outs.push_back(o);
+        }
+      }
+      while ((t.jobs.size() - job0) % t.G) t.jobs.push_back(GateJob{kSlotFalse, kSlotFalse, 0, 0, 0, 0});
+      for (size_t g = job0; g < t.jobs.size(); g += t.G) t.grp_bsk.push_back(cl.bsk);
+      while ((t.outs.size() - out0) % t.tile) t.outs.push_back(GateOut{int32_t(job0), -1, kSlotSink, 0});
+      for (size_t o = out0; o < t.outs.size(); o += t.tile) t.tile_ksk.push_back(cl.ksk);
+    }
+    // the padded batch may need more blocks than the unpadded estimate
+    const size_t groups = t.jobs.size() / t.G;
+    t.blocks = int(std::min<size_t>(groups, size_t(ctx->sms) * (t.G == 1 ? 2 : 1)));
+    return CE_OK;
+  }
+
+  // Stages descriptors in pinned memory and copies them to the device.
+  ce_status stage(const TickDesc &t, cudaStream_t st, uint8_t **dev, size_t *offs) {
+    size_t off = 0;
+    offs[0] = off;
+    off = align16(off + t.jobs.size() * sizeof(GateJob));
+    offs[1] = off;
+    off = align16(off + t.outs.size() * sizeof(GateOut));
+    offs[2] = off;
+    off = align16(off + t.grp_bsk.size() * sizeof(void *));
+    offs[3] = off;
+    off = align16(off + t.tile_ksk.size() * sizeof(void *));
+    const int b = desc_i;
+    desc_i ^= 1;
+    cudaError_t e = cudaEventSynchronize(desc_ev[b]);  // previous use of this buffer copied
+    if (e != cudaSuccess) return cuda_error(e, "engine stage");
+    if (off > desc_cap[b]) {
+      if (h_desc[b]) cudaFreeHost(h_desc[b]);
+      cudaFree(d_desc[b]);
+      h_desc[b] = nullptr;
+      d_desc[b] = nullptr;
+      size_t c = std::max<size_t>(off, 1 << 16) * 2;
+      e = cudaMallocHost(&h_desc[b], c);
+      if (e == cudaSuccess) e = cudaMalloc(&d_desc[b], c);
+      if (e != cudaSuccess) {
+        desc_cap[b] = 0;
+        return set_error(CE_ENOMEM, "engine: descriptor buffers");
+      }
+      desc_cap[b] = c;
+    }
+    std::memcpy(h_desc[b] + offs[0], t.jobs.data(), t.jobs.size() * sizeof(GateJob));
+    std::memcpy(h_desc[b] + offs[1], t.outs.data(), t.outs.size() * sizeof(GateOut));
+    std::memcpy(h_desc[b] + offs[2], t.grp_bsk.data(), t.grp_bsk.size() * sizeof(void *));
+    std::memcpy(h_desc[b] + offs[3], t.tile_ksk.data(), t.tile_ksk.size() * sizeof(void *));
+    e = cudaMemcpyAsync(d_desc[b], h_desc[b], off, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(desc_ev[b], st);
+    if (e != cudaSuccess) return cuda_error(e, "engine stage copy");
+    *dev = d_desc[b];
+    return CE_OK;
+  }
+
+  // Launches one level: gather + linear combination, blind rotation, key
+  // switching into the arena.
+  ce_status launch_level(const GateJob *jobs, int n_jobs, const GateOut *outs, int n_outs,
+                         const uint64_t *const *grp_bsk, const uint32_t *const *tile_ksk, int G,
+                         int blocks, int tile, int jsplit, cudaStream_t st, int *launches) {
+    ce_status s = ensure_job_scratch(ctx, n_jobs);
+    if (s != CE_OK) return s;
+    cudaError_t e = timed(ctx, 0, st, [&] {
+      return launch_lincomb_gather(jobs, arena, ctx->abar, n_jobs, ctx->err, st);
+    });
+    if (e == cudaSuccess)
+      e = timed(ctx, 1, st, [&] {
+        return launch_blind_rotate(nullptr, ctx->abar, ctx->acc, n_jobs, ctx->tw, ctx->err, G,
+                                   blocks, st, grp_bsk);
+      });
+    if (e == cudaSuccess && jsplit > 1) e = launch_zero_slots(outs, arena, n_outs, st);
+    if (e == cudaSuccess)
+      e = timed(ctx, 2, st, [&] {
+        return launch_extract_keyswitch_ex(ctx->acc, nullptr, tile_ksk, outs, arena, n_outs, 2,
+                                           tile, jsplit, st);
+      });
+    if (e != cudaSuccess) return cuda_error(e, "engine level launch");
+    *launches += 3 + (jsplit > 1 ? 1 : 0);
+    return CE_OK;
+  }
+
+  ce_status tick(std::vector<Instance *> &act, cudaStream_t st, int *launches) {
+    TickDesc t;
+    ce_status s = build_tick(act, t);
+    if (s != CE_OK) return s;
+    uint8_t *dev;
+    size_t offs[4];
+    s = stage(t, st, &dev, offs);
+    if (s != CE_OK) return s;
+    s = launch_level(reinterpret_cast<const GateJob *>(dev + offs[0]), int(t.jobs.size()),
+                     reinterpret_cast<const GateOut *>(dev + offs[1]), int(t.outs.size()),
+                     reinterpret_cast<const uint64_t *const *>(dev + offs[2]),
+                     reinterpret_cast<const uint32_t *const *>(dev + offs[3]), t.G, t.blocks,
+                     t.tile, t.jsplit, st, launches);
+    if (s != CE_OK) return s;
+    for (Instance *in : act) ++in->level;
+    return CE_OK;
+  }
+
+  // ------------------------------------------------------------- plans ---
+  void drop_graph(Plan &p) {
+    if (p.exec) cudaGraphExecDestroy(p.exec);
+    p.exec = nullptr;
+  }
+  void drop_plan(Plan &p) {
+    drop_graph(p);
+    cudaFree(p.d_desc);
+    p.d_desc = nullptr;
+    for (uint32_t sl : p.slots) unref(SRef{sl, false});
+    p.slots.clear();
+  }
+
+  ce_status make_plan(int unit, int cond, int client, size_t n, const uint32_t *d_in,
+                      uint32_t *d_out, Plan **out) {
+    for (auto &p : plans)
+      if (p->unit == unit && p->cond == cond && p->client == client && p->n == n &&
+          p->d_in == d_in && p->d_out == d_out) {
+        p->last_use = ++use_clock;
+        *out = p.get();
+        return CE_OK;
+      }
+    const Netlist *net = netlist(unit, cond);
+    if (!net) return set_error(CE_EINVAL, "engine: bad unit");
+    if (plans.size() >= 8) {  // evict the least recently used plan
+      auto lru = std::min_element(plans.begin(), plans.end(), [](const auto &a, const auto &b) {
+        return a->last_use < b->last_use;
+      });
+      drop_plan(**lru);
+      plans.erase(lru);
+    }
+    auto p = std::make_unique<Plan>();
+    p->unit = unit;
+    p->cond = cond;
+    p->client = client;
+    p->n = n;
+    p->d_in = d_in;
+    p->d_out = d_out;
+    p->n_in = net->n_inputs;
+    p->n_out = int(net->outputs.size());
+    // input slots: one consecutive block, so copy-in needs no map
+    const size_t n_in_slots = n * p->n_in;
+    ce_status s = reserve(next_slot + n_in_slots + 1);
+    if (s != CE_OK) return s;
+    p->in_base = uint32_t(next_slot);
+    for (size_t k = 0; k < n_in_slots; ++k) {
+      const uint32_t sl = uint32_t(next_slot++);
+      if (rc.size() <= sl) rc.resize(sl + 1, 0);
+      rc[sl] = 1;  // owned by the plan
+      p->slots.push_back(sl);
+    }
+    std::vector<Instance> inst(n);
+    for (size_t i = 0; i < n; ++i) {
+      std::vector<SRef> in(p->n_in);
+      for (int k = 0; k < p->n_in; ++k) in[k] = SRef{uint32_t(p->in_base + i * p->n_in + k), false};
+      start(inst[i], net, client, in);
+    }
+    std::vector<Instance *> act;
+    for (auto &x : inst) act.push_back(&x);
+    // descriptors of every level, appended to one blob
+    std::vector<uint8_t> blob;
+    auto put = [&](const void *src, size_t bytes) {
+      const size_t off = align16(blob.size());
+      blob.resize(off + bytes);
+      if (bytes) std::memcpy(blob.data() + off, src, bytes);
+      return off;
+    };
+    for (int L = 0; L < net->depth; ++L) {
+      TickDesc t;
+      s = build_tick(act, t);
+      if (s != CE_OK) return s;
+      for (Instance *in : act) ++in->level;
+      Plan::Level lv{};
+      lv.n_jobs = int(t.jobs.size());
+      lv.n_outs = int(t.outs.size());
+      lv.G = t.G;
+      lv.blocks = t.blocks;
+      lv.tile = t.tile;
+      lv.jsplit = t.jsplit;
+      p->max_jobs = std::max(p->max_jobs, t.jobs.size());
+      lv.jobs_off = put(t.jobs.data(), t.jobs.size() * sizeof(GateJob));
+      lv.outs_off = put(t.outs.data(), t.outs.size() * sizeof(GateOut));
+      lv.bsk_off = put(t.grp_bsk.data(), t.grp_bsk.size() * sizeof(void *));
+      lv.ksk_off = put(t.tile_ksk.data(), t.tile_ksk.size() * sizeof(void *));
+      // the plan keeps every slot its levels write (taken before the
+      // instances release theirs below)
+      for (const GateOut &o : t.outs)
+        if (o.slot > kSlotSink) {
+          ref(SRef{o.slot, false});
+          p->slots.push_back(o.slot);
+        }
+      p->levels.push_back(lv);
+    }
+    std::vector<uint32_t> map;
+    for (auto &x : inst) {
+      complete(x);
+      for (const SRef &r : x.result) {
+        map.push_back(r.slot);
+        map.push_back(r.neg ? 1u : 0u);
+        if (r.slot > kSlotSink) p->slots.push_back(r.slot);  // reference taken by complete()
+      }
+    }
+    p->map_off = put(map.data(), map.size() * sizeof(uint32_t));
+    cudaError_t e = cudaMalloc(&p->d_desc, blob.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->d_desc, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_error(e, "engine plan upload");
+    p->last_use = ++use_clock;
+    *out = p.get();
+    plans.push_back(std::move(p));
+    return CE_OK;
+  }
+
+  ce_status run_plan(Plan &p, cudaStream_t st, int *launches) {
+    ce_status s = ensure_job_scratch(ctx, p.max_jobs);
+    if (s != CE_OK) return s;
+    copy_in_kernel<<<unsigned(p.n * p.n_in), 128, 0, st>>>(p.d_in, arena, p.in_base);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "copy_in");
+    ++*launches;
+    for (size_t L = 0; L < p.levels.size(); ++L) {
+      const Plan::Level &lv = p.levels[L];
+      s = launch_level(reinterpret_cast<const GateJob *>(p.d_desc + lv.jobs_off), lv.n_jobs,
+                       reinterpret_cast<const GateOut *>(p.d_desc + lv.outs_off), lv.n_outs,
+                       reinterpret_cast<const uint64_t *const *>(p.d_desc + lv.bsk_off),
+                       reinterpret_cast<const uint32_t *const *>(p.d_desc + lv.ksk_off),
+                       lv.G, lv.blocks, lv.tile, lv.jsplit, st, launches);
+      if (s != CE_OK) return s;
+    }
+    copy_out_kernel<<<unsigned(p.n * p.n_out), 128, 0, st>>>(
+        reinterpret_cast<const uint32_t *>(p.d_desc + p.map_off), arena, p.d_out);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "copy_out");
+    ++*launches;
+    return CE_OK;
+  }
+
+  ce_status eval_unit(int unit, int cond, int client, const uint32_t *d_in, uint32_t *d_out,
+                      size_t n, cudaStream_t st, int *launches) {
+    Plan *p;
+    ce_status s = make_plan(unit, cond, client, n, d_in, d_out, &p);
+    if (s != CE_OK) return s;
+    if (!use_graphs || ctx->profile) return run_plan(*p, st, launches);
+    if (!p->exec) {
+      // capture once on the engine's own stream, then replay on any stream
+      s = ensure_job_scratch(ctx, p->max_jobs);
+      if (s != CE_OK) return s;
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeRelaxed);
+      if (e != cudaSuccess) return cuda_error(e, "begin capture");
+      int dummy = 0;
+      s = run_plan(*p, cap_stream, &dummy);
+      e = cudaStreamEndCapture(cap_stream, &g);
+      if (s != CE_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_error(e, "graph instantiate");
+      p->graph_launches = dummy;
+    }
+    cudaError_t e = cudaGraphLaunch(p->exec, st);
+    if (e != cudaSuccess) return cuda_error(e, "graph launch");
+    *launches += p->graph_launches;
+    return CE_OK;
+  }
+
+  ce_ctx *ctx;
+  uint32_t *arena = nullptr;
+  size_t cap = 0, next_slot = 0;
+  std::vector<uint32_t> rc, free_;
+  std::map<int, Netlist> nets;
+  std::map<int, RegFile> rf;
+  uint8_t *h_desc[2] = {nullptr, nullptr}, *d_desc[2] = {nullptr, nullptr};
+  size_t desc_cap[2] = {0, 0};
+  cudaEvent_t desc_ev[2] = {nullptr, nullptr};
+  int desc_i = 0;
+  std::list<std::unique_ptr<Plan>> plans;
+  uint64_t use_clock = 0;
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;
+};
+
+void engine_destroy(Engine *e) { delete e; }
+void engine_drop_client(Engine *e, int client) {
+  if (e) e->drop_client(client);
+}
+
+namespace {
+
+ce_status get_engine(ce_ctx *ctx, Engine **out) {
+  if (!ctx->engine) {
+    Engine *e = new Engine(ctx);
+    ce_status s = e->init();
+    if (s != CE_OK) {
+      delete e;
+      return s;
+    }
+    ctx->engine = e;
+  }
+  *out = ctx->engine;
+  return CE_OK;
+}
+
+bool live_client(ce_ctx *ctx, int client) {
+  return client >= 0 && client < int(ctx->clients.size()) && ctx->clients[client].live;
+}
+
+// Instruction set (16-bit registers R0..R7, encrypted NZCV).
+enum Opcode : uint8_t {
+  kAdd = 0, kSub = 1, kAnd = 2, kOrr = 3, kLsl = 4, kLslImm = 5, kMul = 6, kUdiv = 7,
+  kCmp = 8, kCsel = 9, kMov = 10, kMovImm = 11, kOpcodes = 12
+};
+
+int unit_of(uint8_t op) {
+  switch (op) {
+    case kAdd: return kUnitAdd;
+    case kSub: return kUnitSub;
+    case kAnd: return kUnitAnd;
+    case kOrr: return kUnitOrr;
+    case kLsl: return kUnitLsl;
+    case kMul: return kUnitMul;
+    case kUdiv: return kUnitUdiv;
+    case kCmp: return kUnitCmp;
+    case kCsel: return kUnitCsel;
+    default: return -1;
+  }
+}
+
+struct Run {
+  int client = 0;
+  const ce_insn *code = nullptr;
+  size_t n = 0, pc = 0;
+  std::unique_ptr<Instance> cur;
+};
+
+// Executes free instructions until one needs gates (started as an instance)
+// or the program ends.
+ce_status advance(Engine &E, Run &r) {
+  RegFile &R = E.regs(r.client);
+  while (!r.cur && r.pc < r.n) {
+    const ce_insn &I = r.code[r.pc];
+    if (I.op >= kOpcodes || I.rd >= kRegs || I.rn >= kRegs || I.rm >= kRegs || I.cond > 13)
+      return set_error(CE_EINVAL, "ce_exec: malformed instruction at index " + std::to_string(r.pc));
+    if (I.op == kLslImm || I.op == kMov || I.op == kMovImm) {
+      SRef nv[kWidth];
+      for (int j = 0; j < kWidth; ++j) {
+        if (I.op == kMov) nv[j] = R.r[I.rn][j];
+        else if (I.op == kMovImm) nv[j] = SRef{kSlotFalse, bool((I.imm >> j) & 1)};
+        else {
+          const int sh = I.imm % kWidth;
+          nv[j] = j >= sh ? R.r[I.rn][j - sh] : SRef{kSlotFalse, false};
+        }
+        E.ref(nv[j]);
+      }
+      for (int j = 0; j < kWidth; ++j) {
+        E.unref(R.r[I.rd][j]);
+        R.r[I.rd][j] = nv[j];
+      }
+      ++r.pc;
+      continue;
+    }
+    const Netlist *net = E.netlist(unit_of(I.op), I.cond);
+    std::vector<SRef> in;
+    for (int j = 0; j < kWidth; ++j) in.push_back(R.r[I.rn][j]);
+    for (int j = 0; j < kWidth; ++j) in.push_back(R.r[I.rm][j]);
+    if (I.op == kCsel)
+      for (int k = 0; k < 4; ++k) in.push_back(R.nzcv[k]);
+    r.cur.reset(new Instance());
+    E.start(*r.cur, net, r.client, in);
+  }
+  return CE_OK;
+}
+
+void retire(Engine &E, Run &r) {
+  const ce_insn &I = r.code[r.pc];
+  E.complete(*r.cur);
+  RegFile &R = E.regs(r.client);
+  if (I.op == kCmp) {
+    for (int k = 0; k < 4; ++k) {
+      E.unref(R.nzcv[k]);
+      R.nzcv[k] = r.cur->result[k];
+    }
+  } else {
+    for (int j = 0; j < kWidth; ++j) {
+      E.unref(R.r[I.rd][j]);
+      R.r[I.rd][j] = r.cur->result[j];
+    }
+  }
+  r.cur.reset();
+  ++r.pc;
+}
+
+}  // namespace
+
+ce_status exec_programs(ce_ctx *ctx, size_t n_prog, const int *clients, const ce_insn *const *progs,
+                        const size_t *lens, uint64_t timeout_ns, cudaStream_t st, int *ticks) {
+  Engine *E;
+  ce_status s = get_engine(ctx, &E);
+  if (s != CE_OK) return s;
+  std::vector<Run> runs(n_prog);
+  for (size_t i = 0; i < n_prog; ++i) {
+    if (!live_client(ctx, clients[i])) return set_error(CE_ENOTFOUND, "ce_exec: unknown client");
+    if (lens[i] && !progs[i]) return set_error(CE_EINVAL, "ce_exec: null program");
+    runs[i].client = clients[i];
+    runs[i].code = progs[i];
+    runs[i].n = lens[i];
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  int launches = 0;
+  *ticks = 0;
+  // On an error return, release what unfinished instructions hold.
+  struct Cleanup {
+    Engine *E;
+    std::vector<Run> *runs;
+    ~Cleanup() {
+      for (Run &r : *runs)
+        if (r.cur) {
+          if (!r.cur->wire.empty()) E->complete(*r.cur);
+          for (const SRef &x : r.cur->result) E->unref(x);
+          r.cur.reset();
+        }
+    }
+  } cleanup{E, &runs};
+  for (;;) {
+    std::vector<Instance *> act;
+    for (Run &r : runs) {
+      s = advance(*E, r);
+      if (s != CE_OK) return s;
+      if (r.cur) act.push_back(r.cur.get());
+    }
+    if (act.empty()) break;
+    s = E->tick(act, st, &launches);
+    if (s != CE_OK) return s;
+    ++*ticks;
+    for (Run &r : runs)
+      if (r.cur && r.cur->level == r.cur->net->depth) retire(*E, r);
+    if (timeout_ns) {
+      const auto dt = std::chrono::steady_clock::now() - t0;
+      if (uint64_t(std::chrono::duration_cast<std::chrono::nanoseconds>(dt).count()) > timeout_ns)
+        return set_error(CE_ETIMEOUT, "ce_exec: timeout");
+    }
+  }
+  ctx->last_launches = launches;
+  return CE_OK;
+}
+
+}  // namespace ce
+
+using namespace ce;
+
+extern "C" ce_status ce_unit_eval_device(ce_ctx *ctx, int client, int unit, int cond,
+                                         const uint32_t *d_in, uint32_t *d_out, size_t n,
+                                         void *cuda_stream) {
+  if (!ctx) return set_error(CE_EINVAL, "ce_unit_eval_device: null context");
+  if (unit < 0 || unit >= kUnitCount || cond < 0 || cond > 13)
+    return set_error(CE_EINVAL, "ce_unit_eval_device: bad unit or condition");
+  if (!live_client(ctx, client)) return set_error(CE_ENOTFOUND, "ce_unit_eval_device: unknown client");
+  if (n == 0) {
+    ctx->last_launches = 0;
+    return CE_OK;
+  }
+  if (!d_in || !d_out) return set_error(CE_EINVAL, "ce_unit_eval_device: null buffer");
+  if (n > (size_t(1) << 20)) return set_error(CE_EINVAL, "ce_unit_eval_device: n too large");
+  Engine *E;
+  ce_status s = get_engine(ctx, &E);
+  if (s != CE_OK) return s;
+  cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
+  int launches = 0;
+  s = E->eval_unit(unit, cond, client, d_in, d_out, n, st, &launches);
+  ctx->last_launches = launches;
+  return s;
+}
+
+extern "C" ce_status ce_set_unit_graphs(ce_ctx *ctx, int on) {
+  if (!ctx) return set_error(CE_EINVAL, "ce_set_unit_graphs: null context");
+  Engine *E;
+  ce_status s = get_engine(ctx, &E);
+  if (s != CE_OK) return s;
+  E->use_graphs = on != 0;
+  return CE_OK;
+}
+
+extern "C" ce_status ce_reg_write(ce_ctx *ctx, int client, int reg, const ce_lwe *bits) {
+  if (!ctx || !bits || reg < 0 || reg >= kRegs) return set_error(CE_EINVAL, "ce_reg_write: bad argument");
+  if (!live_client(ctx, client)) return set_error(CE_ENOTFOUND, "ce_reg_write: unknown client");
+  Engine *E;
+  ce_status s = get_engine(ctx, &E);
+  if (s != CE_OK) return s;
+  RegFile &R = E->regs(client);
+  uint32_t sl[kWidth];
+  for (int j = 0; j < kWidth; ++j) {
+    s = E->alloc(&sl[j]);
+    if (s != CE_OK) return s;
+  }
+  cudaError_t e = cudaSuccess;
+  for (int j = 0; j < kWidth && e == cudaSuccess; ++j)
+    e = cudaMemcpyAsync(E->arena + size_t(sl[j]) * kSlotWords, &bits[j], sizeof(ce_lwe),
+                        cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  for (int j = 0; j < kWidth; ++j) {
+    E->unref(R.r[reg][j]);
+    R.r[reg][j] = SRef{sl[j], false};
+  }
+  return e == cudaSuccess ? CE_OK : cuda_error(e, "ce_reg_write");
+}
+
+static ce_status read_refs(ce_ctx *ctx, Engine *E, const SRef *refs, int count, ce_lwe *out) {
+  cudaError_t e = cudaDeviceSynchronize();
+  for (int j = 0; j < count && e == cudaSuccess; ++j)
+    e = cudaMemcpy(&out[j], E->arena + size_t(refs[j].slot) * kSlotWords, sizeof(ce_lwe),
+                   cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_error(e, "register read");
+  for (int j = 0; j < count; ++j)
+    if (refs[j].neg) {
+      for (int m = 0; m < kLweN; ++m) out[j].a[m] = 0u - out[j].a[m];
+      out[j].b = 0u - out[j].b;
+    }
+  return CE_OK;
+}
+
+extern "C" ce_status ce_reg_read(ce_ctx *ctx, int client, int reg, ce_lwe *bits) {
+  if (!ctx || !bits || reg < 0 || reg >= kRegs) return set_error(CE_EINVAL, "ce_reg_read: bad argument");
+  if (!live_client(ctx, client)) return set_error(CE_ENOTFOUND, "ce_reg_read: unknown client");
+  Engine *E;
+  ce_status s = get_engine(ctx, &E);
+  if (s != CE_OK) return s;
+  return read_refs(ctx, E, E->regs(client).r[reg], kWidth, bits);
+}
+
+extern "C" ce_status ce_flags_read(ce_ctx *ctx, int client, ce_lwe *nzcv) {
+  if (!ctx || !nzcv) return set_error(CE_EINVAL, "ce_flags_read: bad argument");
+  if (!live_client(ctx, client)) return set_error(CE_ENOTFOUND, "ce_flags_read: unknown client");
+  Engine *E;
+  ce_status s = get_engine(ctx, &E);
+  if (s != CE_OK) return s;
+  return read_refs(ctx, E, E->regs(client).nzcv, 4, nzcv);
+}
+
+extern "C" ce_status ce_exec(ce_ctx *ctx, int client, const ce_insn *prog, size_t n,
+                             uint64_t timeout_ns) {
+  if (!ctx) return set_error(CE_EINVAL, "ce_exec: null context");
+  int ticks = 0;
+  return exec_programs(ctx, 1, &client, &prog, &n, timeout_ns, ctx->stream, &ticks);
+}
+
+extern "C" ce_status ce_exec_multi(ce_ctx *ctx, size_t n_programs, const int *clients,
+                                   const ce_insn *const *progs, const size_t *lens,
+                                   uint64_t timeout_ns) {
+  if (!ctx || (n_programs && (!clients || !progs || !lens)))
+    return set_error(CE_EINVAL, "ce_exec_multi: bad argument");
+  int ticks = 0;
+  return exec_programs(ctx, n_programs, clients, progs, lens, timeout_ns, ctx->stream, &ticks);
+}

@@ -13,12 +13,35 @@ namespace ce {
 cudaError_t launch_lincomb_modswitch(const uint8_t *ops, const uint32_t *a, const uint32_t *b,
                                      const uint32_t *c, uint16_t *abar, int n_jobs, int mode,
                                      int *err, cudaStream_t st);
+// grp_bsk (optional): per gate-group key (group g = gates [g*G, g*G+G)).
 cudaError_t launch_blind_rotate(const uint64_t *bsk, const uint16_t *abar, uint32_t *acc,
                                 int n_jobs, const uint64_t *tw, int *err, int gates_per_block,
-                                int blocks, cudaStream_t st);
+                                int blocks, cudaStream_t st,
+                                const uint64_t *const *grp_bsk = nullptr);
 size_t blind_rotate_smem_bytes(int gates_per_block);
 cudaError_t launch_extract_keyswitch(const uint32_t *acc, const uint32_t *ksk, uint32_t *out,
                                      int n_out, bool mux, int tile, int jsplit, cudaStream_t st);
+// Netlist-engine descriptors.  A ciphertext slot of the engine's arena is
+// kSlotWords uint32 (a[500], b, padding).
+struct GateJob {
+  uint32_t a, b;        // arena slots of the two inputs
+  uint8_t op;           // 0..9 gate, 10/11 MUX halves
+  uint8_t neg_a, neg_b;
+  uint8_t pad;
+};
+struct GateOut {
+  int32_t job1, job2;   // accumulators (job2 >= 0: MUX, adds (0, +1/8))
+  uint32_t slot;        // arena slot written
+  uint32_t pad;
+};
+cudaError_t launch_lincomb_gather(const GateJob *jobs, const uint32_t *arena, uint16_t *abar,
+                                  int n_jobs, int *err, cudaStream_t st);
+// mode 0: packed outputs, one job each; 1: MUX pairs; 2: descriptors to the arena.
+cudaError_t launch_extract_keyswitch_ex(const uint32_t *acc, const uint32_t *ksk,
+                                        const uint32_t *const *tile_ksk, const GateOut *outs,
+                                        uint32_t *out, int n_out, int mode, int tile, int jsplit,
+                                        cudaStream_t st);
+cudaError_t launch_zero_slots(const GateOut *outs, uint32_t *arena, int n_out, cudaStream_t st);
 cudaError_t launch_bsk_to_transform(const uint32_t *bsk, uint64_t *out, const uint64_t *tw,
                                     cudaStream_t st);
 cudaError_t launch_negacyclic_mul(const int16_t *d, const uint32_t *k, uint32_t *out, int n,

@@ -1,0 +1,105 @@
+"""Encrypted register programs (ce_exec / ce_exec_multi) against a plaintext
+model of the same 16-bit ARM-subset machine; several programs and two
+clients advance together; malformed programs, unknown clients and the host
+timeout are errors, not crashes."""
+import numpy as np
+import pytest
+
+from gpu_common import MASTER_SEED, ce, ctx, keys  # noqa: F401
+from oracle import netlists as NL
+
+pytestmark = pytest.mark.gpu
+W, M = 16, 0xFFFF
+
+
+def run_plain(prog, regs, nzcv=0):
+    regs = list(regs)
+    for op, rd, rn, rm, imm, cond in prog:
+        a, b = regs[rn], regs[rm]
+        if op == "CMP":
+            N, Z, C, V = NL.armv8("CMP", a, b, W)
+            nzcv = N | Z << 1 | C << 2 | V << 3
+        elif op == "CSEL":
+            regs[rd] = NL.armv8("CSEL", a, b, W, cond, nzcv)
+        elif op == "LSL_IMM":
+            regs[rd] = (a << (imm % W)) & M
+        elif op == "MOV":
+            regs[rd] = a
+        elif op == "MOV_IMM":
+            regs[rd] = imm
+        else:
+            regs[rd] = NL.armv8(op, a, b, W)
+    return regs, nzcv
+
+
+def random_program(rng, length):
+    ops = ["ADD", "SUB", "AND", "ORR", "LSL", "LSL_IMM", "CMP", "CSEL", "MOV", "MOV_IMM"]
+    prog = [("CMP", 0, 1, 2, 0, 0)]           # flags defined before any CSEL
+    while len(prog) < length:
+        op = ops[rng.integers(len(ops))]
+        prog.append((op, int(rng.integers(8)), int(rng.integers(8)), int(rng.integers(8)),
+                     int(rng.integers(256)), int(rng.integers(14))))
+    return prog
+
+
+def load_regs(ce, c, cid, sk, vals, seed):
+    for r, v in enumerate(vals):
+        bits = np.stack([ce.ce_encrypt_bit(sk, (v >> j) & 1, seed, 16 * r + j) for j in range(W)])
+        ce.ce_reg_write(c, cid, r, bits)
+
+
+def read_regs(ce, c, cid, sk):
+    return [NL.from_bits([ce.ce_decrypt_bit(sk, x) for x in ce.ce_reg_read(c, cid, r)])
+            for r in range(8)]
+
+
+@pytest.fixture(scope="module")
+def second_client(ce, ctx):
+    c, _ = ctx
+    sk2 = ce.ce_secret_keygen(MASTER_SEED + 1)
+    ck2 = ce.ce_cloud_keygen(sk2, MASTER_SEED + 1)
+    cid2 = ce.ce_client_admit(c, ck2)
+    yield sk2, cid2
+    ce.ce_client_evict(c, cid2)
+
+
+def test_programs_two_clients(ce, ctx, keys, second_client):
+    c, cid = ctx
+    sk, _ = keys
+    sk2, cid2 = second_client
+    rng = np.random.default_rng(2021)
+    # one program per client (each client has one register file)
+    progs = [random_program(rng, int(rng.integers(8, 17))) for _ in range(2)]
+    init = [[int(x) for x in rng.integers(0, 1 << W, 8)] for _ in range(2)]
+    load_regs(ce, c, cid, sk, init[0], 40)
+    load_regs(ce, c, cid2, sk2, init[1], 41)
+    ce.ce_exec_multi(c, [cid, cid2], [[ce.insn(*i) for i in p] for p in progs])
+    for (sk_, cid_), p, r0 in zip(((sk, cid), (sk2, cid2)), progs, init):
+        exp_regs, exp_nzcv = run_plain(p, r0)
+        assert read_regs(ce, c, cid_, sk_) == exp_regs
+        flags = [ce.ce_decrypt_bit(sk_, x) for x in ce.ce_flags_read(c, cid_)]
+        assert flags == [(exp_nzcv >> k) & 1 for k in range(4)]
+
+
+def test_mul_udiv_program(ce, ctx, keys):
+    c, cid = ctx
+    sk, _ = keys
+    init = [1234, 56, 0, 7, 65535, 3, 0, 9]
+    prog = [("MUL", 2, 0, 1, 0, 0), ("UDIV", 6, 4, 3, 0, 0), ("UDIV", 7, 0, 6, 0, 0)]
+    load_regs(ce, c, cid, sk, init, 42)
+    ce.ce_exec(c, cid, [ce.insn(*i) for i in prog])
+    assert read_regs(ce, c, cid, sk) == run_plain(prog, init)[0]
+
+
+def test_program_errors(ce, ctx):
+    c, cid = ctx
+    with pytest.raises(ce.CeError) as ei:
+        ce.ce_exec(c, cid, [ce.insn("ADD", 9, 0, 0)])          # register out of range
+    assert ei.value.code == -1
+    with pytest.raises(ce.CeError) as ei:
+        ce.ce_exec(c, 999, [ce.insn("ADD", 0, 0, 0)])
+    assert ei.value.code == -6
+    with pytest.raises(ce.CeError) as ei:                       # host-side timeout
+        ce.ce_exec(c, cid, [ce.insn("ADD", 0, 1, 2)] * 4, timeout_ns=1)
+    assert ei.value.code == -4
+    ce.ce_synchronize(c)

@@ -262,9 +262,18 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
         uint64_t v[16], Y[2][8];
         const int sh = 22 - 10 * pz;
 #pragma unroll
-        for (int n2 = 0; n2 < 16; ++n2)
-          v[n2] = gl::from_i32(int32_t((w[n2] >> sh) & 1023u) - 512);
-        ntt::forward(v, Y, buf, t, 1, kThreads, tw_fwd);
+        for (int n2 = 0; n2 < 16; ++n2) {
+          const int32_t dgt = int32_t((w[n2] >> sh) & 1023u) - 512;
+          // Negacyclic pre-twist psi^(64 n2) = 2^(6 n2) applied to the small
+          // digit directly: |d| 2^(6 n2) < 2^63 for n2 <= 9 needs no reduction.
+          if (n2 <= 9) {
+            const uint64_t mag = static_cast<uint64_t>(dgt < 0 ? -dgt : dgt) << (6 * n2);
+            v[n2] = dgt < 0 ? gl::kP - mag : mag;
+          } else {
+            v[n2] = gl::mul_pow2(gl::from_i32(dgt), 6 * n2);
+          }
+        }
+        ntt::forward_pretwisted(v, Y, buf, t, 1, kThreads, tw_fwd);
         wait_slot(smem_u32(full + slot), uint32_t(chunk / NSLOT) & 1u, abort, err);
         // X[o] += Y[0] * key(c=0, p, o) + Y[1] * key(c=1, p, o)
         const uint64_t *key = ring + size_t(slot) * kChunkWords + t;
@@ -274,7 +283,7 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
           for (int o = 0; o < 2; ++o) {
             const uint64_t k0 = key[((0 * 2 + o) * 8 + d) * 128];
             const uint64_t k1 = key[((1 * 2 + o) * 8 + d) * 128];
-            X[o][d] = gl::add(X[o][d], gl::add(gl::mul(Y[0][d], k0), gl::mul(Y[1][d], k1)));
+            X[o][d] = gl::add(X[o][d], gl::mul2_add(Y[0][d], k0, Y[1][d], k1));
           }
         }
         // Release the slot; the last warp out refills it with chunk + NSLOT.

@@ -72,12 +72,11 @@ __device__ __forceinline__ void dft(uint64_t (&v)[M]) {
 
 // ------------------------------------------------------------ forward ---
 
-// Phase A: thread (P, n1) = (t >> 6, t & 63) holds v[n2] = x_P[n1 + 64 n2].
+// Phase A: thread (P, n1) = (t >> 6, t & 63) holds v[n2] = x_P[n1 + 64 n2]
+// already multiplied by the negacyclic pre-twist 2^(6 n2).
 __device__ __forceinline__ void fwd_phase_a(uint64_t (&v)[16], uint64_t *buf, int t,
                                             const uint64_t *__restrict__ tw_fwd) {
   const int P = t >> 6, n1 = t & 63;
-#pragma unroll
-  for (int n2 = 1; n2 < 16; ++n2) v[n2] = gl::mul_pow2(v[n2], 6 * n2);
   dft<16, 12>(v);
   uint64_t *col = buf + P * 16 * kRow + n1;
 #pragma unroll
@@ -87,20 +86,20 @@ __device__ __forceinline__ void fwd_phase_a(uint64_t (&v)[16], uint64_t *buf, in
 // Phase C1 for warp wg of the group: lane -> (P, k2) = (lane >> 4, lane & 15),
 // a in {2 wg, 2 wg + 1}.  a is warp-uniform, so the shift of the twiddle
 // 8^(a c) is the same across the warp (uniform branches, one code copy).
-__device__ __forceinline__ void fwd_phase_c1(uint64_t *buf, int wg, int lane, int bar, int nthr) {
+// The thread reads positions a + 8 b and writes positions 8 c + a of its row:
+// the same eight positions, touched by no other thread, so the transform is
+// done in place one a at a time without a barrier in between.
+__device__ __forceinline__ void fwd_phase_c1(uint64_t *buf, int wg, int lane) {
   uint64_t *row = buf + ((lane >> 4) * 16 + (lane & 15)) * kRow;
-  uint64_t u[2][8];
-#pragma unroll
-  for (int j = 0; j < 2; ++j)
-#pragma unroll
-    for (int b = 0; b < 8; ++b) u[j][b] = row[2 * wg + j + 8 * b];
-  named_bar(bar, nthr);  // every read of this phase precedes every write
-#pragma unroll
+#pragma unroll 1
   for (int j = 0; j < 2; ++j) {
-    dft<8, 24>(u[j]);
     const int a = 2 * wg + j;
+    uint64_t u[8];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) row[c * 8 + a] = gl::mul_pow2_uniform(u[j][c], (3 * a * c) % 192);
+    for (int b = 0; b < 8; ++b) u[b] = row[a + 8 * b];
+    dft<8, 24>(u);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) row[c * 8 + a] = gl::mul_pow2_uniform(u[c], (3 * a * c) % 192);
   }
 }
 
@@ -117,16 +116,26 @@ __device__ __forceinline__ void fwd_phase_c2(uint64_t (&X)[2][8], const uint64_t
 }
 
 // Forward transform of two polynomials; v holds the phase-A inputs of this
-// thread (clobbered), X receives the eight positions of each polynomial.
-__device__ __forceinline__ void forward(uint64_t (&v)[16], uint64_t (&X)[2][8], uint64_t *buf,
-                                        int t, int bar, int nthr,
-                                        const uint64_t *__restrict__ tw_fwd) {
+// thread, already pre-twisted (clobbered); X receives the eight positions
+// of each polynomial.
+__device__ __forceinline__ void forward_pretwisted(uint64_t (&v)[16], uint64_t (&X)[2][8],
+                                                   uint64_t *buf, int t, int bar, int nthr,
+                                                   const uint64_t *__restrict__ tw_fwd) {
   named_bar(bar, nthr);  // the buffer is free
   fwd_phase_a(v, buf, t, tw_fwd);
   named_bar(bar, nthr);
-  fwd_phase_c1(buf, t >> 5, t & 31, bar, nthr);
+  fwd_phase_c1(buf, t >> 5, t & 31);
   named_bar(bar, nthr);
   fwd_phase_c2(X, buf, t);
+}
+
+// Forward transform of untwisted inputs v[n2] = x_P[n1 + 64 n2].
+__device__ __forceinline__ void forward(uint64_t (&v)[16], uint64_t (&X)[2][8], uint64_t *buf,
+                                        int t, int bar, int nthr,
+                                        const uint64_t *__restrict__ tw_fwd) {
+#pragma unroll
+  for (int n2 = 1; n2 < 16; ++n2) v[n2] = gl::mul_pow2(v[n2], 6 * n2);
+  forward_pretwisted(v, X, buf, t, bar, nthr, tw_fwd);
 }
 
 // ------------------------------------------------------------ inverse ---
@@ -142,23 +151,18 @@ __device__ __forceinline__ void inv_phase_c2(uint64_t (&X)[2][8], uint64_t *buf,
   }
 }
 
-__device__ __forceinline__ void inv_phase_c1(uint64_t *buf, int wg, int lane, int bar, int nthr) {
+__device__ __forceinline__ void inv_phase_c1(uint64_t *buf, int wg, int lane) {
   uint64_t *row = buf + ((lane >> 4) * 16 + (lane & 15)) * kRow;
-  uint64_t u[2][8];
-#pragma unroll
+#pragma unroll 1
   for (int j = 0; j < 2; ++j) {
     const int a = 2 * wg + j;
+    uint64_t u[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c)
-      u[j][c] = gl::mul_pow2_uniform(row[c * 8 + a], (192 - (3 * a * c) % 192) % 192);
-  }
-  named_bar(bar, nthr);
+      u[c] = gl::mul_pow2_uniform(row[c * 8 + a], (192 - (3 * a * c) % 192) % 192);
+    dft<8, 168>(u);
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    dft<8, 168>(u[j]);
-    const int a = 2 * wg + j;
-#pragma unroll
-    for (int b = 0; b < 8; ++b) row[a + 8 * b] = u[j][b];
+    for (int b = 0; b < 8; ++b) row[a + 8 * b] = u[b];
   }
 }
 
@@ -181,7 +185,7 @@ __device__ __forceinline__ void inverse(uint64_t (&X)[2][8], uint64_t (&v)[16], 
   named_bar(bar, nthr);
   inv_phase_c2(X, buf, t);
   named_bar(bar, nthr);
-  inv_phase_c1(buf, t >> 5, t & 31, bar, nthr);
+  inv_phase_c1(buf, t >> 5, t & 31);
   named_bar(bar, nthr);
   inv_phase_a(v, buf, t, tw_inv);
 }

@@ -255,6 +255,33 @@ ce_status ce_exec(ce_ctx *ctx, int client, const ce_insn *prog, size_t n, uint64
 ce_status ce_exec_multi(ce_ctx *ctx, size_t n_programs, const int *clients,
                         const ce_insn *const *progs, const size_t *lens, uint64_t timeout_ns);
 
+/* ---------------------------------------------------------------- serving --- */
+
+/* A serving loop on a context (§4 cloud service model): requests are single
+ * instructions (ce_insn) on a client's encrypted registers, submitted from
+ * any host thread.  A worker thread batches them continuously: each tick
+ * starts queued requests (one in flight per client, so each client's
+ * requests run in submission order, at most max_inflight in total; 0 = no
+ * limit), runs one level of every in-flight instruction of every client in
+ * one batched launch, and retires finished ones.  Requests arriving while
+ * others run join at the next tick.  Results are bit-identical to running
+ * the same instruction alone.  While a server runs, other calls on the same
+ * context are serialised with it. */
+typedef struct ce_server ce_server;
+ce_status ce_server_create(ce_ctx *ctx, int max_inflight, ce_server **out);
+/* Enqueue one instruction for `client`; *ticket identifies the request. */
+ce_status ce_server_submit(ce_server *s, int client, const ce_insn *insn, uint64_t *ticket);
+/* Non-blocking status; times are steady-clock nanoseconds (submission,
+ * start on the GPU path, completion of its GPU work). */
+ce_status ce_server_poll(ce_server *s, uint64_t ticket, int *done, uint64_t *submit_ns,
+                         uint64_t *start_ns, uint64_t *done_ns);
+/* Wait for a request (timeout_ns = 0: no limit; CE_ETIMEOUT on expiry). */
+ce_status ce_server_wait(ce_server *s, uint64_t ticket, uint64_t timeout_ns);
+ce_status ce_server_stats(ce_server *s, uint64_t *ticks, uint64_t *bootstraps,
+                          uint64_t *queued, uint64_t *running);
+/* Finishes every submitted request, then stops the worker. */
+void ce_server_destroy(ce_server *s);
+
 /* The paper has no counterpart to this call.  Same as ce_gates_batch_device
  * (same kernels, same results) but it allocates no device memory: for
  * callers that cannot let the library call cudaMalloc, e.g. a serving loop

@@ -79,6 +79,14 @@ def lib() -> ctypes.CDLL:
         "ce_flags_read": (i32, [vp, i32, vp]),
         "ce_exec": (i32, [vp, i32, vp, sz, u64]),
         "ce_exec_multi": (i32, [vp, sz, vp, vp, vp, u64]),
+        "ce_server_create": (i32, [vp, i32, pp]),
+        "ce_server_submit": (i32, [vp, i32, vp, ctypes.POINTER(u64)]),
+        "ce_server_poll": (i32, [vp, u64, ctypes.POINTER(i32), ctypes.POINTER(u64),
+                                 ctypes.POINTER(u64), ctypes.POINTER(u64)]),
+        "ce_server_wait": (i32, [vp, u64, u64]),
+        "ce_server_stats": (i32, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
+                                  ctypes.POINTER(u64), ctypes.POINTER(u64)]),
+        "ce_server_destroy": (None, [vp]),
         "ce_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), i32]),
     }
     for name, (res, args) in sig.items():
@@ -412,3 +420,51 @@ def ce_exec_multi(ctx: Context, clients, progs, timeout_ns: int = 0):
     ptrs = (ctypes.c_void_p * len(progs))(*[ctypes.addressof(a) for a, _ in arrs])
     lens = (ctypes.c_size_t * len(progs))(*[n for _, n in arrs])
     _check(lib().ce_exec_multi(ctx.ptr, len(progs), cl, ptrs, lens, timeout_ns), "ce_exec_multi")
+
+
+class Server:
+    def __init__(self, ptr: int):
+        self.ptr = ptr
+
+    def close(self):
+        if getattr(self, "ptr", None) and _L is not None:
+            _L.ce_server_destroy(self.ptr)
+        self.ptr = None
+
+    def __del__(self):
+        self.close()
+
+
+def ce_server_create(ctx: Context, max_inflight: int = 0) -> Server:
+    p = ctypes.c_void_p()
+    _check(lib().ce_server_create(ctx.ptr, max_inflight, ctypes.byref(p)), "ce_server_create")
+    return Server(p.value)
+
+
+def ce_server_submit(srv: Server, client: int, ins: Insn) -> int:
+    t = ctypes.c_uint64()
+    _check(lib().ce_server_submit(srv.ptr, client, ctypes.byref(ins), ctypes.byref(t)),
+           "ce_server_submit")
+    return t.value
+
+
+def ce_server_poll(srv: Server, ticket: int) -> dict:
+    d = ctypes.c_int()
+    a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().ce_server_poll(srv.ptr, ticket, ctypes.byref(d), ctypes.byref(a), ctypes.byref(b),
+                                ctypes.byref(c)), "ce_server_poll")
+    return {"done": bool(d.value), "submit_ns": a.value, "start_ns": b.value, "done_ns": c.value}
+
+
+def ce_server_wait(srv: Server, ticket: int, timeout_ns: int = 0):
+    _check(lib().ce_server_wait(srv.ptr, ticket, timeout_ns), "ce_server_wait")
+
+
+def ce_server_stats(srv: Server) -> dict:
+    v = [ctypes.c_uint64() for _ in range(4)]
+    _check(lib().ce_server_stats(srv.ptr, *[ctypes.byref(x) for x in v]), "ce_server_stats")
+    return dict(zip(["ticks", "bootstraps", "queued", "running"], [x.value for x in v]))
+
+
+def ce_server_destroy(srv: Server):
+    srv.close()

@@ -16,8 +16,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcryptoemu.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["bootstrap_kernels.cu", "api.cu", "noalloc.cu", "engine.cu", "host_keys.cpp",
-           "netlist.cpp", "units_host.cpp"]
+SOURCES = ["bootstrap_kernels.cu", "api.cu", "noalloc.cu", "engine.cu", "serve.cu",
+           "host_keys.cpp", "netlist.cpp", "units_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
@@ -49,7 +49,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
         return LIB
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = [NVCC, "-shared", "-o", tmp] + objs + ARCH + ["-lpthread"]

@@ -22,6 +22,7 @@
 #include <list>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -573,11 +574,21 @@ class Engine {
   uint64_t use_clock = 0;
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;
+  // one host thread at a time inside the engine (a serving thread and
+  // register reads of other threads may meet here)
+  std::recursive_mutex mu;
 };
 
-void engine_destroy(Engine *e) { delete e; }
+void serve_runs_forget(Engine *e);
+void engine_destroy(Engine *e) {
+  if (!e) return;
+  serve_runs_forget(e);
+  delete e;
+}
 void engine_drop_client(Engine *e, int client) {
-  if (e) e->drop_client(client);
+  if (!e) return;
+  std::lock_guard<std::recursive_mutex> lock(e->mu);
+  e->drop_client(client);
 }
 
 namespace {
@@ -626,7 +637,11 @@ struct Run {
   const ce_insn *code = nullptr;
   size_t n = 0, pc = 0;
   std::unique_ptr<Instance> cur;
+  ce_insn one{};  // storage for single-instruction runs (serving)
 };
+
+// In-flight single instructions of the serving loop, by client.
+std::map<Engine *, std::map<int, Run>> g_serve_runs;
 
 // Executes free instructions until one needs gates (started as an instance)
 // or the program ends.
@@ -687,11 +702,81 @@ void retire(Engine &E, Run &r) {
 
 }  // namespace
 
+void serve_runs_forget(Engine *e) {
+  auto it = g_serve_runs.find(e);
+  if (it == g_serve_runs.end()) return;
+  for (auto &kv : it->second)
+    if (kv.second.cur) {
+      e->complete(*kv.second.cur);
+      for (const SRef &x : kv.second.cur->result) e->unref(x);
+    }
+  g_serve_runs.erase(it);
+}
+
+int gates_at_level(const Instance &in) {
+  const Netlist &n = *in.net;
+  int k = 0;
+  for (int g = n.level_begin[in.level]; g < n.level_begin[in.level + 1]; ++g)
+    k += n.gates[g].op == kOpMux ? 2 : 1;
+  return k;
+}
+
+ce_status engine_serve_tick(ce_ctx *ctx, cudaStream_t st, const std::vector<int> &start_clients,
+                            const std::vector<ce_insn> &start_insns, std::vector<int> &retired,
+                            int *active_after, int *bootstraps) {
+  Engine *E;
+  ce_status s = get_engine(ctx, &E);
+  if (s != CE_OK) return s;
+  std::lock_guard<std::recursive_mutex> lock(E->mu);
+  auto &runs = g_serve_runs[E];
+  for (size_t i = 0; i < start_clients.size(); ++i) {
+    Run &r = runs[start_clients[i]];
+    r = Run();
+    r.client = start_clients[i];
+    r.one = start_insns[i];
+    r.code = &r.one;
+    r.n = 1;
+    s = advance(*E, r);
+    if (s != CE_OK) {
+      runs.erase(start_clients[i]);
+      return s;
+    }
+    if (!r.cur) {  // no bootstrap needed: done now
+      retired.push_back(r.client);
+      runs.erase(start_clients[i]);
+    }
+  }
+  std::vector<Instance *> act;
+  int boots = 0;
+  for (auto &kv : runs) {
+    act.push_back(kv.second.cur.get());
+    boots += gates_at_level(*kv.second.cur);
+  }
+  if (!act.empty()) {
+    int launches = 0;
+    s = E->tick(act, st, &launches);
+    if (s != CE_OK) return s;
+  }
+  for (auto it = runs.begin(); it != runs.end();) {
+    if (it->second.cur->level == it->second.cur->net->depth) {
+      retire(*E, it->second);
+      retired.push_back(it->first);
+      it = runs.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  *active_after = int(runs.size());
+  *bootstraps = boots;
+  return CE_OK;
+}
+
 ce_status exec_programs(ce_ctx *ctx, size_t n_prog, const int *clients, const ce_insn *const *progs,
                         const size_t *lens, uint64_t timeout_ns, cudaStream_t st, int *ticks) {
   Engine *E;
   ce_status s = get_engine(ctx, &E);
   if (s != CE_OK) return s;
+  std::lock_guard<std::recursive_mutex> lock(E->mu);
   std::vector<Run> runs(n_prog);
   for (size_t i = 0; i < n_prog; ++i) {
     if (!live_client(ctx, clients[i])) return set_error(CE_ENOTFOUND, "ce_exec: unknown client");
@@ -761,6 +846,7 @@ extern "C" ce_status ce_unit_eval_device(ce_ctx *ctx, int client, int unit, int 
   if (s != CE_OK) return s;
   cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
   int launches = 0;
+  std::lock_guard<std::recursive_mutex> lock(E->mu);
   s = E->eval_unit(unit, cond, client, d_in, d_out, n, st, &launches);
   ctx->last_launches = launches;
   return s;
@@ -781,6 +867,7 @@ extern "C" ce_status ce_reg_write(ce_ctx *ctx, int client, int reg, const ce_lwe
   Engine *E;
   ce_status s = get_engine(ctx, &E);
   if (s != CE_OK) return s;
+  std::lock_guard<std::recursive_mutex> lock(E->mu);
   RegFile &R = E->regs(client);
   uint32_t sl[kWidth];
   for (int j = 0; j < kWidth; ++j) {
@@ -799,7 +886,10 @@ extern "C" ce_status ce_reg_write(ce_ctx *ctx, int client, int reg, const ce_lwe
   return e == cudaSuccess ? CE_OK : cuda_error(e, "ce_reg_write");
 }
 
-static ce_status read_refs(ce_ctx *ctx, Engine *E, const SRef *refs, int count, ce_lwe *out) {
+static ce_status read_refs(ce_ctx *ctx, Engine *E, const SRef *refs_in, int count, ce_lwe *out) {
+  std::lock_guard<std::recursive_mutex> lock(E->mu);
+  SRef refs[kWidth];
+  for (int j = 0; j < count; ++j) refs[j] = refs_in[j];
   cudaError_t e = cudaDeviceSynchronize();
   for (int j = 0; j < count && e == cudaSuccess; ++j)
     e = cudaMemcpy(&out[j], E->arena + size_t(refs[j].slot) * kSlotWords, sizeof(ce_lwe),
@@ -819,6 +909,7 @@ extern "C" ce_status ce_reg_read(ce_ctx *ctx, int client, int reg, ce_lwe *bits)
   Engine *E;
   ce_status s = get_engine(ctx, &E);
   if (s != CE_OK) return s;
+  std::lock_guard<std::recursive_mutex> lock(E->mu);
   return read_refs(ctx, E, E->regs(client).r[reg], kWidth, bits);
 }
 
@@ -828,6 +919,7 @@ extern "C" ce_status ce_flags_read(ce_ctx *ctx, int client, ce_lwe *nzcv) {
   Engine *E;
   ce_status s = get_engine(ctx, &E);
   if (s != CE_OK) return s;
+  std::lock_guard<std::recursive_mutex> lock(E->mu);
   return read_refs(ctx, E, E->regs(client).nzcv, 4, nzcv);
 }
 

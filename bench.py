@@ -251,6 +251,7 @@ def run_ours(args, rank: int, world: int, local: int):
     stream = torch.cuda.current_stream(dev)
     ctx = ce.ce_create(local, 0, stream)
     cid = ce.ce_client_admit(ctx, ck)
+    tuned = ce.ce_autotune(ctx, cid)              # launch shapes measured on this device
     gates_per_add = ce.ce_unit_info("ADD")["n_bootstraps"]
     boots = n * gates_per_add
 
@@ -378,7 +379,8 @@ def run_ours(args, rank: int, world: int, local: int):
                            "bootstraps_per_step": boots, "levels": 9,
                            "l2": "flushed between steps (256 MB write)",
                            "parallelism": f"independent batches x{world}",
-                           "graph_replay_gates_per_s": graph_value},
+                           "graph_replay_gates_per_s": graph_value,
+                           "autotuned_gates_per_block": tuned},
                 "latency_ms": {"add16_batch256_p50": pct(step_ms, 50),
                                "add16_batch256_p99": pct(step_ms, 99),
                                "mul16_batch64_p50": pct(mul_ms, 50),

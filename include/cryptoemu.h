@@ -171,6 +171,12 @@ ce_status ce_set_blind_rotate_config(ce_ctx *ctx, int gates_per_block,
  * asynchronous calls since the previous check (CE_ETIMEOUT when a bounded
  * device wait expired). */
 ce_status ce_synchronize(ce_ctx *ctx);
+/* Project autotuner: times the blind-rotation kernel with 1, 2 and 4 gates
+ * per block at a ladder of batch sizes (1 .. 9728 gates, synthetic inputs,
+ * the client's key) and keeps the fastest shape per size; later launches
+ * with the automatic shape use the nearest measured size.  Writes up to cap
+ * (size, gates per block) pairs and their count.  Takes a few seconds. */
+ce_status ce_autotune(ce_ctx *ctx, int client, int *out_jobs, int *out_g, int cap, int *count);
 /* Number of kernels the last ce_gates_batch[_device] / ce_mux_batch_device
  * call launched (for launch accounting). */
 int ce_last_launch_count(ce_ctx *ctx);

@@ -87,6 +87,7 @@ def lib() -> ctypes.CDLL:
         "ce_server_stats": (i32, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
                                   ctypes.POINTER(u64), ctypes.POINTER(u64)]),
         "ce_server_destroy": (None, [vp]),
+        "ce_autotune": (i32, [vp, i32, vp, vp, i32, ctypes.POINTER(i32)]),
         "ce_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), i32]),
     }
     for name, (res, args) in sig.items():
@@ -468,3 +469,12 @@ def ce_server_stats(srv: Server) -> dict:
 
 def ce_server_destroy(srv: Server):
     srv.close()
+
+
+def ce_autotune(ctx: Context, client: int) -> dict:
+    """Measure and install the fastest blind-rotation shape per batch size."""
+    jobs = (ctypes.c_int * 32)()
+    g = (ctypes.c_int * 32)()
+    n = ctypes.c_int()
+    _check(lib().ce_autotune(ctx.ptr, client, jobs, g, 32, ctypes.byref(n)), "ce_autotune")
+    return {int(jobs[i]): int(g[i]) for i in range(n.value)}

@@ -1,6 +1,7 @@
 // C ABI of the library: contexts, client admission, batched gates.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -121,6 +122,19 @@ Client *find_client(ce_ctx *ctx, int id) {
 // Blind-rotation launch shape: gates per block and resident blocks per SM.
 void br_config(const ce_ctx *ctx, size_t jobs, int *G, int *blocks) {
   int g = ctx->cfg_g, bps = ctx->cfg_bps;
+  if (g == 0 && !ctx->tune_jobs.empty()) {
+    // autotuned: the shape measured fastest at the nearest job count (log scale)
+    size_t best = 0;
+    double bd = 1e30;
+    for (size_t i = 0; i < ctx->tune_jobs.size(); ++i) {
+      const double d = std::fabs(std::log(double(jobs) + 1) - std::log(double(ctx->tune_jobs[i]) + 1));
+      if (d < bd) {
+        bd = d;
+        best = i;
+      }
+    }
+    g = ctx->tune_g[best];
+  }
   if (g == 0) {
     if (jobs >= size_t(8) * ctx->sms) g = 4;
     else if (jobs >= size_t(2) * ctx->sms) g = 2;
@@ -505,3 +519,74 @@ cudaEvent_t take_event(ce_ctx *ctx) {
 }
 
 }  // namespace ce
+
+// Autotuner: times the blind-rotation kernel with 1, 2 and 4 gates per block
+// at a ladder of job counts (on the client's key, synthetic inputs) and keeps
+// the fastest shape per count; later launches use the nearest measured count.
+extern "C" ce_status ce_autotune(ce_ctx *ctx, int client, int *out_jobs, int *out_g, int cap,
+                                 int *count) {
+  if (!ctx) return set_error(CE_EINVAL, "ce_autotune: null context");
+  Client *cl = find_client(ctx, client);
+  if (!cl) return set_error(CE_ENOTFOUND, "ce_autotune: unknown client");
+  const int ladder[] = {1, 8, 38, 76, 152, 304, 608, 1216, 2432, 4864, 9728};
+  const int nl = int(sizeof(ladder) / sizeof(ladder[0]));
+  ce_status s = ensure_jobs(ctx, size_t(ladder[nl - 1]));
+  if (s != CE_OK) return s;
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = ctx->stream;
+  // synthetic modulus-switched inputs (uniform in [0, 2048))
+  std::vector<uint16_t> h(size_t(ladder[nl - 1]) * kAbarStride);
+  uint32_t x = 0x9E3779B9u;
+  for (auto &v : h) {
+    x ^= x << 13;
+    x ^= x >> 17;
+    x ^= x << 5;
+    v = uint16_t(x & 2047u);
+  }
+  cudaError_t e = cudaMemcpyAsync(ctx->abar, h.data(), h.size() * sizeof(uint16_t),
+                                  cudaMemcpyHostToDevice, st);
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  std::vector<int> tj, tg;
+  const int saved_g = ctx->cfg_g, saved_bps = ctx->cfg_bps;
+  for (int i = 0; i < nl && e == cudaSuccess; ++i) {
+    float best = 1e30f;
+    int best_g = 1;
+    for (int g : {1, 2, 4}) {
+      ctx->cfg_g = g;
+      ctx->cfg_bps = 0;
+      int G, blocks;
+      br_config(ctx, size_t(ladder[i]), &G, &blocks);
+      float ms = 0.f;
+      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // first run warms up
+        e = cudaEventRecord(a, st);
+        if (e == cudaSuccess)
+          e = launch_blind_rotate(cl->bsk, ctx->abar, ctx->acc, ladder[i], ctx->tw, ctx->err, G,
+                                  blocks, st);
+        if (e == cudaSuccess) e = cudaEventRecord(b, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      }
+      if (e == cudaSuccess && ms < best) {
+        best = ms;
+        best_g = g;
+      }
+    }
+    tj.push_back(ladder[i]);
+    tg.push_back(best_g);
+  }
+  ctx->cfg_g = saved_g;
+  ctx->cfg_bps = saved_bps;
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (e != cudaSuccess) return cuda_fail(e, "ce_autotune");
+  ctx->tune_jobs = tj;
+  ctx->tune_g = tg;
+  if (count) *count = int(tj.size());
+  for (int i = 0; i < int(tj.size()) && i < cap; ++i) {
+    if (out_jobs) out_jobs[i] = tj[i];
+    if (out_g) out_g[i] = tg[i];
+  }
+  return check_device_error(ctx);
+}

@@ -48,6 +48,8 @@ struct ce_ctx {
   struct Timed { int kind; cudaEvent_t a, b; };
   std::vector<Timed> timed;
   ce::Engine *engine = nullptr;
+  // Autotuned blind-rotation shape: gates per block for measured job counts.
+  std::vector<int> tune_jobs, tune_g;
 };
 
 namespace ce {

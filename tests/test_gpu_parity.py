@@ -152,3 +152,17 @@ def test_empty_batch_and_errors(ce, ctx):
     ce.ce_synchronize(c)                        # the flag was consumed
     with pytest.raises(ce.CeError):
         ce.ce_set_blind_rotate_config(c, 3, 0)
+
+
+def test_autotuner_installs_shapes_and_keeps_results(ce, ctx, O, full_keys):
+    import numpy as np
+    from gpu_common import random_ciphertexts, run_gates_device
+    c, cid = ctx
+    rng = np.random.default_rng(55)
+    ops = rng.integers(0, 10, 40)
+    a, b = random_ciphertexts(rng, 40), random_ciphertexts(rng, 40)
+    before = run_gates_device(ce, ctx, ops, a, b)
+    table = ce.ce_autotune(c, cid)
+    assert set(table.values()) <= {1, 2, 4} and min(table) == 1 and max(table) >= 9728
+    after = run_gates_device(ce, ctx, ops, a, b)
+    assert (before == after).all()

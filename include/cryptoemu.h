@@ -163,16 +163,18 @@ ce_status ce_negacyclic_mul_device(ce_ctx *ctx, const int16_t *d_d,
                                    const uint32_t *d_k, uint32_t *d_out,
                                    size_t n, void *cuda_stream);
 
-/* Tuning of the blind-rotation launch: gates per block (1, 2 or 4) and
- * resident blocks per SM; 0 = autotuned choice.  Applies to later calls. */
+/* Tuning of the blind-rotation launch: gates per block (1, 2 or 4, or 3 for
+ * the latency shape: one gate per block whose three thread groups transform
+ * the three gadget levels concurrently) and resident blocks per SM; 0 =
+ * autotuned choice.  Applies to later calls. */
 ce_status ce_set_blind_rotate_config(ce_ctx *ctx, int gates_per_block,
                                      int blocks_per_sm);
 /* Waits for the context's stream and reports a device-side failure of the
  * asynchronous calls since the previous check (CE_ETIMEOUT when a bounded
  * device wait expired). */
 ce_status ce_synchronize(ce_ctx *ctx);
-/* Project autotuner: times the blind-rotation kernel with 1, 2 and 4 gates
- * per block at a ladder of batch sizes (1 .. 9728 gates, synthetic inputs,
+/* Project autotuner: times the blind-rotation kernel in each launch shape
+ * (1, 2, 4 gates per block and the one-gate three-group shape) at a ladder of batch sizes (1 .. 9728 gates, synthetic inputs,
  * the client's key) and keeps the fastest shape per size; later launches
  * with the automatic shape use the nearest measured size.  Writes up to cap
  * (size, gates per block) pairs and their count.  Takes a few seconds. */

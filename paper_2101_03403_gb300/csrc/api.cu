@@ -141,7 +141,8 @@ void br_config(const ce_ctx *ctx, size_t jobs, int *G, int *blocks) {
     else g = 1;
   }
   if (bps == 0) bps = (g == 1) ? 2 : 1;
-  const size_t groups = (jobs + g - 1) / g;
+  const int per_block = g == 3 ? 1 : g;  // shape 3: one gate, three groups
+  const size_t groups = (jobs + per_block - 1) / per_block;
   size_t b = size_t(ctx->sms) * bps;
   if (groups < b) b = groups;
   *G = g;
@@ -425,9 +426,9 @@ extern "C" ce_status ce_negacyclic_mul_device(ce_ctx *ctx, const int16_t *d_d,
 extern "C" ce_status ce_set_blind_rotate_config(ce_ctx *ctx, int gates_per_block,
                                                 int blocks_per_sm) {
   if (!ctx) return set_error(CE_EINVAL, "ce_set_blind_rotate_config: null context");
-  if (!(gates_per_block == 0 || gates_per_block == 1 || gates_per_block == 2 ||
-        gates_per_block == 4))
-    return set_error(CE_EINVAL, "gates_per_block must be 0, 1, 2 or 4");
+  if (gates_per_block < 0 || gates_per_block > 4)
+    return set_error(CE_EINVAL, "gates_per_block must be 0 (auto), 1, 2, 3 (one gate, three "
+                                "groups) or 4");
   const int max_bps = gates_per_block == 1 ? 2 : 1;
   if (blocks_per_sm < 0 || (gates_per_block && blocks_per_sm > max_bps))
     return set_error(CE_EINVAL, "blocks_per_sm exceeds what shared memory allows");
@@ -553,7 +554,7 @@ extern "C" ce_status ce_autotune(ce_ctx *ctx, int client, int *out_jobs, int *ou
   for (int i = 0; i < nl && e == cudaSuccess; ++i) {
     float best = 1e30f;
     int best_g = 1;
-    for (int g : {1, 2, 4}) {
+    for (int g : {1, 2, 3, 4}) {
       ctx->cfg_g = g;
       ctx->cfg_bps = 0;
       int G, blocks;

@@ -318,6 +318,134 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
   }
 }
 
+// Latency-oriented blind rotation: one gate per block, three 128-thread
+// groups.  In each CMux step group g forward-transforms gadget level g of
+// both accumulator halves and multiplies by its key chunk (kept in its own
+// shared-memory slot, refilled by bulk copy for the next step right after
+// use); groups 1 and 2 hand their partial sums to group 0 through shared
+// memory, and group 0 runs the inverse transform and updates ACC.  The step's
+// critical path is one forward transform, one exchange and one inverse
+// instead of three forward transforms and one inverse.
+struct WideSmem {
+  static constexpr size_t kSlots = size_t(3) * kChunkWords * 8;
+  static constexpr size_t kAcc = 2 * kRingN * 4;
+  static constexpr size_t kBufs = size_t(3) * ntt::kBufWords * 8;
+  static constexpr size_t kXch = size_t(2) * 2 * 8 * 128 * 8;
+  static constexpr size_t kTotal = kSlots + kAcc + kBufs + kXch + 64;
+};
+
+__global__ void __launch_bounds__(384, 1) blind_rotate_wide_kernel(
+    const uint64_t *__restrict__ bsk, const uint64_t *const *__restrict__ gate_bsk,
+    const uint16_t *__restrict__ abar, uint32_t *__restrict__ acc_out, int n_jobs,
+    const uint64_t *__restrict__ tw, int *__restrict__ err) {
+  using L = WideSmem;
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint64_t *slots = reinterpret_cast<uint64_t *>(smem);
+  uint32_t *acc = reinterpret_cast<uint32_t *>(smem + L::kSlots);
+  uint64_t *bufs = reinterpret_cast<uint64_t *>(smem + L::kSlots + L::kAcc);
+  uint64_t *xch = reinterpret_cast<uint64_t *>(smem + L::kSlots + L::kAcc + L::kBufs);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::kSlots + L::kAcc + L::kBufs + L::kXch);
+  volatile int *abort = reinterpret_cast<volatile int *>(full + 3);
+  const int g = threadIdx.x >> 7, t = threadIdx.x & 127;
+  uint64_t *buf = bufs + g * ntt::kBufWords;
+  uint64_t *slot = slots + size_t(g) * kChunkWords;
+  const uint64_t *tw_fwd = tw, *tw_inv = tw + 1024;
+  const int my_gates = int(blockIdx.x) < n_jobs ? (n_jobs - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
+  const int total = my_gates * kLweN;  // chunks per group
+  auto chunk_src = [&](int c) {
+    const int gate = blockIdx.x + (c / kLweN) * gridDim.x;
+    const uint64_t *key = gate_bsk ? gate_bsk[gate] : bsk;
+    return key + (size_t(c % kLweN) * kGadgetL + g) * kChunkWords;
+  };
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 3; ++k)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(full + k)) : "memory");
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (t == 0 && total > 0) issue_chunk(slot, smem_u32(full + g), chunk_src(0));
+  const int P = t >> 6, n1 = t & 63;
+  int c = 0;
+  for (int jg = 0; jg < my_gates; ++jg) {
+    const int job = blockIdx.x + jg * gridDim.x;
+    const uint16_t *ab = abar + size_t(job) * kAbarStride;
+    {
+      const int bbar = ab[kLweN];
+      const int k = (2 * kRingN - bbar) & (2 * kRingN - 1);
+      for (int j = threadIdx.x; j < kRingN; j += 384) {
+        acc[j] = 0;
+        const bool hi = k < kRingN ? (j >= k) : (j < k - kRingN);
+        acc[kRingN + j] = hi ? kMuEighth : 0u - kMuEighth;
+      }
+    }
+    __syncthreads();
+    for (int i = 0; i < kLweN; ++i, ++c) {
+      const int rot = __ldg(ab + i);
+      uint64_t v[16], Y[2][8];
+      {
+        const uint32_t *src = acc + P * kRingN;
+        const int kk = rot & (kRingN - 1);
+        const uint32_t flip = (rot >= kRingN) ? 0xFFFFFFFFu : 0u;
+        const int sh = 22 - 10 * g;
+#pragma unroll
+        for (int n2 = 0; n2 < 16; ++n2) {
+          const int n = n1 + 64 * n2;
+          const int sidx = n - kk;
+          uint32_t r = sidx >= 0 ? src[sidx] : 0u - src[sidx + kRingN];
+          r = (r ^ flip) - flip;
+          const uint32_t wv = r - src[n] + kDecompOffset;
+          const int32_t dgt = int32_t((wv >> sh) & 1023u) - 512;
+          if (n2 <= 9) {
+            const uint64_t mag = static_cast<uint64_t>(dgt < 0 ? -dgt : dgt) << (6 * n2);
+            v[n2] = dgt < 0 ? gl::kP - mag : mag;
+          } else {
+            v[n2] = gl::mul_pow2(gl::from_i32(dgt), 6 * n2);
+          }
+        }
+      }
+      ntt::forward_pretwisted(v, Y, buf, t, 1 + g, 128, tw_fwd);
+      wait_slot(smem_u32(full + g), uint32_t(c) & 1u, abort, err);
+      uint64_t X[2][8];
+      {
+        const uint64_t *key = slot + t;
+#pragma unroll
+        for (int d = 0; d < 8; ++d)
+#pragma unroll
+          for (int o = 0; o < 2; ++o)
+            X[o][d] = gl::mul2_add(Y[0][d], key[((0 * 2 + o) * 8 + d) * 128], Y[1][d],
+                                   key[((1 * 2 + o) * 8 + d) * 128]);
+      }
+      ntt::named_bar(1 + g, 128);  // the group is done with its slot
+      if (t == 0 && c + 1 < total && !*abort) issue_chunk(slot, smem_u32(full + g), chunk_src(c + 1));
+      if (g > 0) {
+        uint64_t *x = xch + size_t(g - 1) * 2 * 8 * 128 + t;
+#pragma unroll
+        for (int o = 0; o < 2; ++o)
+#pragma unroll
+          for (int d = 0; d < 8; ++d) x[(o * 8 + d) * 128] = X[o][d];
+      }
+      __syncthreads();
+      if (g == 0) {
+        const uint64_t *x1 = xch + t, *x2 = xch + 2 * 8 * 128 + t;
+#pragma unroll
+        for (int o = 0; o < 2; ++o)
+#pragma unroll
+          for (int d = 0; d < 8; ++d)
+            X[o][d] = gl::add(X[o][d], gl::add(x1[(o * 8 + d) * 128], x2[(o * 8 + d) * 128]));
+        ntt::inverse(X, v, buf, t, 1, 128, tw_inv);
+        uint32_t *dst = acc + P * kRingN + n1;
+#pragma unroll
+        for (int n2 = 0; n2 < 16; ++n2) dst[64 * n2] += gl::lift32(v[n2]);
+      }
+      __syncthreads();
+    }
+    uint32_t *out = acc_out + size_t(job) * 2 * kRingN;
+    for (int j = threadIdx.x; j < 2 * kRingN; j += 384) out[j] = acc[j];
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------- K4 ---
 // Fused sample extraction (coefficient 0: a'_0 = A_0, a'_j = -A_{N-j},
 // b' = B_0) and key switching: each a'_j rounded to 16 bits, split into 8
@@ -494,6 +622,7 @@ size_t blind_rotate_smem_bytes(int gates_per_block) {
   switch (gates_per_block) {
     case 1: return BrSmem<1, 2>::kTotal;
     case 2: return BrSmem<2, 3>::kTotal;
+    case 3: return WideSmem::kTotal;
     default: return BrSmem<4, 3>::kTotal;
   }
 }
@@ -513,6 +642,15 @@ cudaError_t launch_blind_rotate(const uint64_t *bsk, const uint16_t *abar, uint3
   switch (gates_per_block) {
     case 1: return launch_br<1, 2>(bsk, grp_bsk, abar, acc, n_jobs, tw, err, blocks, st);
     case 2: return launch_br<2, 3>(bsk, grp_bsk, abar, acc, n_jobs, tw, err, blocks, st);
+    case 3: {  // one gate per block, three cooperating groups
+      cudaError_t e = cudaFuncSetAttribute(blind_rotate_wide_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           int(WideSmem::kTotal));
+      if (e != cudaSuccess) return e;
+      blind_rotate_wide_kernel<<<blocks, 384, WideSmem::kTotal, st>>>(bsk, grp_bsk, abar, acc,
+                                                                      n_jobs, tw, err);
+      return cudaGetLastError();
+    }
     default: return launch_br<4, 3>(bsk, grp_bsk, abar, acc, n_jobs, tw, err, blocks, st);
   }
 }

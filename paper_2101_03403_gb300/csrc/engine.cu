@@ -297,13 +297,14 @@ class Engine {
           t.outs.push_back(o);
         }
       }
-      while ((t.jobs.size() - job0) % t.G) t.jobs.push_back(GateJob{kSlotFalse, kSlotFalse, 0, 0, 0, 0});
-      for (size_t g = job0; g < t.jobs.size(); g += t.G) t.grp_bsk.push_back(cl.bsk);
+      const int gsz = t.G == 3 ? 1 : t.G;  // jobs per key group of the launch shape
+      while ((t.jobs.size() - job0) % gsz) t.jobs.push_back(GateJob{kSlotFalse, kSlotFalse, 0, 0, 0, 0});
+      for (size_t g = job0; g < t.jobs.size(); g += gsz) t.grp_bsk.push_back(cl.bsk);
       while ((t.outs.size() - out0) % t.tile) t.outs.push_back(GateOut{int32_t(job0), -1, kSlotSink, 0});
       for (size_t o = out0; o < t.outs.size(); o += t.tile) t.tile_ksk.push_back(cl.ksk);
     }
     // the padded batch may need more blocks than the unpadded estimate
-    const size_t groups = t.jobs.size() / t.G;
+    const size_t groups = t.jobs.size() / (t.G == 3 ? 1 : t.G);
     t.blocks = int(std::min<size_t>(groups, size_t(ctx->sms) * (t.G == 1 ? 2 : 1)));
     return CE_OK;
   }

@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
           for (int o = 0; o < 2; ++o) {
             const uint64_t k0 = key[((0 * 2 + o) * 8 + d) * 128];
             const uint64_t k1 = key[((1 * 2 + o) * 8 + d) * 128];
-            X[o][d] = gl::add(X[o][d], gl::mul2_add(Y[0][d], k0, Y[1][d], k1));
+            X[o][d] = gl::mac2(X[o][d], Y[0][d], k0, Y[1][d], k1);
           }
         }
         // Release the slot; the last warp out refills it with chunk + NSLOT.

@@ -141,32 +141,60 @@ __device__ __forceinline__ void shl96(uint64_t x, int s, uint32_t &y0, uint32_t 
   y2 = static_cast<uint32_t>(hi >> 32);
 }
 
-// a * b + c * d mod p with one reduction: the two 128-bit products are
-// summed in 129 bits; the carry k (0 or 1) is worth k * 2^128 = -k * 2^32.
-__device__ __forceinline__ uint64_t mul2_add(uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
+// x + a * b + c * d mod p with one reduction: the two 128-bit products and
+// x are summed in 130 bits (carry word k <= 2); with 2^96 = -1 and
+// 2^128 = -2^32 the value is lo - (h1 + k * 2^32) + h0 * eps, where the
+// subtrahend is below 2^34 (one borrow correction) and h0 * eps below
+// 2^64 - eps (one carry correction).
+__device__ __forceinline__ uint64_t mac2(uint64_t x, uint64_t a, uint64_t b, uint64_t c,
+                                         uint64_t d) {
   const uint64_t lo1 = a * b, hi1 = __umul64hi(a, b);
   const uint64_t lo2 = c * d, hi2 = __umul64hi(c, d);
-  uint64_t lo, hi;
-  uint32_t k;
+  uint64_t r;
   asm("{\n\t"
-      ".reg .u32 a0, a1, a2, a3, b0, b1, b2, b3;\n\t"
-      "mov.b64 {a0, a1}, %3;\n\t"
-      "mov.b64 {a2, a3}, %4;\n\t"
-      "mov.b64 {b0, b1}, %5;\n\t"
-      "mov.b64 {b2, b3}, %6;\n\t"
+      ".reg .u32 a0, a1, a2, a3, b0, b1, b2, b3, x0, x1, k, w, z, u0, u1;\n\t"
+      ".reg .u64 u;\n\t"
+      "mov.u32 z, 0;\n\t"
+      "mov.b64 {a0, a1}, %1;\n\t"
+      "mov.b64 {a2, a3}, %2;\n\t"
+      "mov.b64 {b0, b1}, %3;\n\t"
+      "mov.b64 {b2, b3}, %4;\n\t"
+      "mov.b64 {x0, x1}, %5;\n\t"
       "add.cc.u32 a0, a0, b0;\n\t"
       "addc.cc.u32 a1, a1, b1;\n\t"
       "addc.cc.u32 a2, a2, b2;\n\t"
       "addc.cc.u32 a3, a3, b3;\n\t"
-      "addc.u32 %2, 0, 0;\n\t"
+      "addc.u32 k, z, z;\n\t"
+      "add.cc.u32 a0, a0, x0;\n\t"
+      "addc.cc.u32 a1, a1, x1;\n\t"
+      "addc.cc.u32 a2, a2, z;\n\t"
+      "addc.cc.u32 a3, a3, z;\n\t"
+      "addc.u32 k, k, z;\n\t"
+      // t = lo - (a3 + k * 2^32); on borrow add p (= subtract eps)
+      "sub.cc.u32 a0, a0, a3;\n\t"
+      "subc.cc.u32 a1, a1, k;\n\t"
+      "subc.u32 w, z, z;\n\t"
+      "sub.cc.u32 a0, a0, w;\n\t"
+      "subc.u32 a1, a1, z;\n\t"
+      // + a2 * eps
+      "mul.wide.u32 u, a2, 0xFFFFFFFF;\n\t"
+      "mov.b64 {u0, u1}, u;\n\t"
+      "add.cc.u32 a0, a0, u0;\n\t"
+      "addc.cc.u32 a1, a1, u1;\n\t"
+      "addc.u32 w, z, z;\n\t"
+      "mul.lo.u32 w, w, 0xFFFFFFFF;\n\t"
+      "add.cc.u32 a0, a0, w;\n\t"
+      "addc.u32 a1, a1, z;\n\t"
       "mov.b64 %0, {a0, a1};\n\t"
-      "mov.b64 %1, {a2, a3};\n\t"
       "}"
-      : "=l"(lo), "=l"(hi), "=r"(k)
-      : "l"(lo1), "l"(hi1), "l"(lo2), "l"(hi2));
-  const uint64_t r = reduce128(hi, lo);
-  // subtract k * 2^32 (mod p): k * 2^32 < p
-  return k ? sub(r, uint64_t(k) << 32) : r;
+      : "=l"(r)
+      : "l"(lo1), "l"(hi1), "l"(lo2), "l"(hi2), "l"(x));
+  return r;
+}
+
+// a * b + c * d mod p with one reduction.
+__device__ __forceinline__ uint64_t mul2_add(uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
+  return mac2(0, a, b, c, d);
 }
 
 __device__ __forceinline__ uint64_t mul(uint64_t a, uint64_t b) {

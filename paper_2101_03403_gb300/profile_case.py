@@ -2,6 +2,10 @@
 profiling a single launch of each kernel (e.g. under Nsight Compute).
 
   python -m paper_2101_03403_gb300.profile_case --gates 608 [--reps 1] [--gpb 0]
+  python -m paper_2101_03403_gb300.profile_case --unit ADD --pairs 256
+
+The second form runs one eager evaluation of a functional unit on encrypted
+operand pairs (the benchmark's step for ADD with 256 pairs).
 
 Keys come from seed 20210103; inputs are uniform 501-word ciphertexts (the
 bootstrapping path is a fixed function of any input, so timing and
@@ -20,6 +24,8 @@ def main():
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--gpb", type=int, default=0, help="gates per block (0 = autotuned)")
     ap.add_argument("--mux", action="store_true")
+    ap.add_argument("--unit", default=None, help="run a functional unit instead of gates")
+    ap.add_argument("--pairs", type=int, default=256)
     args = ap.parse_args()
     import torch
 
@@ -29,6 +35,24 @@ def main():
     ctx = ce.ce_create(0)
     cid = ce.ce_client_admit(ctx, ck)
     ce.ce_set_blind_rotate_config(ctx, args.gpb, 0)
+    if args.unit:
+        rng = np.random.default_rng(2)
+        info = ce.ce_unit_info(args.unit)
+        n = args.pairs
+        bits = rng.integers(0, 2, (n, info["n_inputs"]))
+        inp = np.zeros((n, info["n_inputs"], 501), np.uint32)
+        for i in range(n):
+            for j in range(info["n_inputs"]):
+                inp[i, j] = ce.ce_encrypt_bit(sk, int(bits[i, j]), 3, i * info["n_inputs"] + j)
+        d_in = torch.from_numpy(inp.view(np.int32)).cuda()
+        d_out = torch.empty((n, info["n_outputs"], 501), dtype=torch.int32, device="cuda")
+        ce.ce_set_unit_graphs(ctx, False)
+        for _ in range(args.reps):
+            ce.ce_unit_eval_device(ctx, cid, args.unit, d_in, d_out, n, 0, torch.cuda.current_stream())
+        ce.ce_synchronize(ctx)
+        print(f"ran {args.reps} x {args.unit} on {n} pairs")
+        ctx.close()
+        return
     n = args.gates
     rng = np.random.default_rng(1)
     a = torch.from_numpy(rng.integers(0, 2 ** 32, (n, 501), dtype=np.uint64)

@@ -151,7 +151,7 @@ def test_empty_batch_and_errors(ce, ctx):
     assert ei.value.code == -1
     ce.ce_synchronize(c)                        # the flag was consumed
     with pytest.raises(ce.CeError):
-        ce.ce_set_blind_rotate_config(c, 3, 0)
+        ce.ce_set_blind_rotate_config(c, 5, 0)      # no such launch shape
 
 
 def test_autotuner_installs_shapes_and_keeps_results(ce, ctx, O, full_keys):

@@ -81,11 +81,12 @@ ce_status ensure_jobs(ce_ctx *ctx, size_t jobs) {
   if (jobs <= ctx->job_cap) return CE_OK;
   size_t cap = ctx->job_cap ? ctx->job_cap : 64;
   while (cap < jobs) cap *= 2;
-  cudaFree(ctx->abar);
+  cudaFree(ctx->abar);  // synchronises with work still using the old scratch
   cudaFree(ctx->acc);
   ctx->abar = nullptr;
   ctx->acc = nullptr;
   ctx->job_cap = 0;
+  ++ctx->scratch_gen;  // captured graphs that baked in the old pointers are stale
   cudaError_t e = cudaMalloc(&ctx->abar, cap * kAbarStride * sizeof(uint16_t));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->acc, cap * 2 * kRingN * sizeof(uint32_t));
   if (e != cudaSuccess) return set_error(CE_ENOMEM, "scratch allocation failed");

@@ -36,6 +36,7 @@ struct ce_ctx {
   uint16_t *abar = nullptr;
   uint32_t *acc = nullptr;
   size_t job_cap = 0;
+  uint64_t scratch_gen = 0;  // bumped whenever abar/acc are reallocated
   uint8_t *io_ops = nullptr;
   uint32_t *io_a = nullptr, *io_b = nullptr, *io_out = nullptr;
   size_t io_cap = 0;

@@ -112,6 +112,7 @@ struct Plan {
   int n_in = 0, n_out = 0;
   size_t max_jobs = 0;
   cudaGraphExec_t exec = nullptr;
+  uint64_t exec_gen = 0;  // scratch generation the graph was captured with
   int graph_launches = 0;
   uint64_t last_use = 0;
 };
@@ -536,10 +537,11 @@ class Engine {
     ce_status s = make_plan(unit, cond, client, n, d_in, d_out, &p);
     if (s != CE_OK) return s;
     if (!use_graphs || ctx->profile) return run_plan(*p, st, launches);
+    s = ensure_job_scratch(ctx, p->max_jobs);
+    if (s != CE_OK) return s;
+    if (p->exec && p->exec_gen != ctx->scratch_gen) drop_graph(*p);  // scratch was replaced
     if (!p->exec) {
       // capture once on the engine's own stream, then replay on any stream
-      s = ensure_job_scratch(ctx, p->max_jobs);
-      if (s != CE_OK) return s;
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeRelaxed);
       if (e != cudaSuccess) return cuda_error(e, "begin capture");
@@ -554,6 +556,7 @@ class Engine {
       if (g) cudaGraphDestroy(g);
       if (e != cudaSuccess) return cuda_error(e, "graph instantiate");
       p->graph_launches = dummy;
+      p->exec_gen = ctx->scratch_gen;
     }
     cudaError_t e = cudaGraphLaunch(p->exec, st);
     if (e != cudaSuccess) return cuda_error(e, "graph launch");

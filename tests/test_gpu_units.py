@@ -124,3 +124,30 @@ def test_unit_ciphertexts_match_oracle(ce, ctx, keys, O, full_keys, unit):
     for k in range(W):
         assert (got[k] == exp[k]).all(), (unit, k)
     assert NL.from_bits(decrypt_all(ce, sk, got[None])[0]) == NL.armv8(unit, 0xBEEF, int(b[0]), W)
+
+
+def test_graph_replay_after_scratch_growth(ce, ctx, keys):
+    """A captured unit graph must not keep using scratch that a larger later
+    call replaced: replay after growth equals a fresh eager evaluation."""
+    import torch
+    from gpu_common import random_ciphertexts, run_gates_device
+    c, cid = ctx
+    sk, _ = keys
+    rng = np.random.default_rng(31)
+    a, b = operands(rng, 8)
+    inp = enc_operands(ce, sk, operand_bits(a, b), 12)
+    d_in = to_dev(inp.view(np.int32))
+    d_out = torch.empty((8, W, 501), dtype=torch.int32, device="cuda")
+    ce.ce_unit_eval_device(c, cid, "ORR", d_in, d_out, 8, 0)      # captures the graph
+    ce.ce_synchronize(c)
+    first = d_out.clone()
+    n = 20000                                                       # grows the scratch
+    ops = rng.integers(0, 10, n)
+    run_gates_device(ce, ctx, ops, random_ciphertexts(rng, n), random_ciphertexts(rng, n))
+    d_out.zero_()
+    ce.ce_unit_eval_device(c, cid, "ORR", d_in, d_out, 8, 0)      # same buffers: replay
+    ce.ce_synchronize(c)
+    assert torch.equal(first, d_out)
+    bits = decrypt_all(ce, sk, d_out.cpu().numpy().view(np.uint32))
+    for i in range(8):
+        assert NL.from_bits(bits[i]) == int(a[i]) | int(b[i])

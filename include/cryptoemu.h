@@ -155,9 +155,12 @@ ce_status ce_mux_batch_device(ce_ctx *ctx, int client, const uint32_t *d_a,
 
 /* Building block of the blind rotation, exposed for verification: n exact
  * negacyclic products out[i] = d[i] * k[i] in Z_{2^32}[X]/(X^1024 + 1), d a
- * polynomial of signed 16-bit coefficients, k of uint32 coefficients, through
- * the same 1024-point transform over p = 2^64 - 2^32 + 1 the blind rotation
- * uses (exact because |sum| < 1024 * 2^15 * 2^32 < p / 2).  Device buffers
+ * polynomial of signed 16-bit coefficients in [-8192, 8192] (the blind
+ * rotation's digits lie in [-512, 511]), k of uint32 coefficients (taken as
+ * signed), through the same two-prime 1024-point transform the blind
+ * rotation uses (primes 2^28 - 2^16 + 1 and 2^28 - 2^16 - 2^11 + 1; exact
+ * because |sum| <= 1024 * 2^13 * 2^31 = 2^54 < p0 p1 / 2; coefficients of d
+ * outside that range give unspecified results).  Device buffers
  * d_d (n x 1024 int16), d_k, d_out (n x 1024 uint32); asynchronous. */
 ce_status ce_negacyclic_mul_device(ce_ctx *ctx, const int16_t *d_d,
                                    const uint32_t *d_k, uint32_t *d_out,

@@ -9,25 +9,13 @@
 
 #include "ce_internal.h"
 #include "launch.h"
+#include "rns_arith.h"
 
 namespace ce {
 
 namespace {
 thread_local std::string g_last_error;
 
-using u128 = unsigned __int128;
-constexpr uint64_t kP = 0xFFFFFFFF00000001ull;
-
-uint64_t mulmod(uint64_t a, uint64_t b) { return uint64_t((u128(a) * b) % kP); }
-uint64_t powmod(uint64_t a, uint64_t e) {
-  uint64_t r = 1;
-  while (e) {
-    if (e & 1) r = mulmod(r, a);
-    a = mulmod(a, a);
-    e >>= 1;
-  }
-  return r;
-}
 }  // namespace
 
 ce_status set_error(ce_status code, const std::string &msg) {
@@ -35,30 +23,26 @@ ce_status set_error(ce_status code, const std::string &msg) {
   return code;
 }
 
-// psi: a primitive 2048-th root of unity of F_p with psi^32 = 8 (so that the
-// 64-, 32- and 8-point sub-transforms use powers of two).  Found from a
-// quadratic non-residue h: h^((p-1)/2048) has order exactly 2048, and among
-// its odd powers the first with 32nd power 8 is taken.
-void transform_tables(uint64_t *out) {
-  uint64_t h = 2;
-  while (powmod(h, (kP - 1) / 2) == 1) ++h;
-  const uint64_t g = powmod(h, (kP - 1) / 2048);
-  uint64_t psi = 0;
-  for (uint64_t j = 1; j < 2048; j += 2) {
-    const uint64_t c = powmod(g, j);
-    if (powmod(c, 32) == 8) {
-      psi = c;
-      break;
-    }
+// Per-thread twist factors of the two-prime transform (rns_ntt.cuh) with
+// their Shoup quotients; the inverse table carries the 1/1024 scale.
+void transform_tables(uint4 *out) {
+  const uint32_t ps[2] = {rns::P<0>(), rns::P<1>()};
+  const uint32_t roots[2] = {rns::Psi<0>(), rns::Psi<1>()};
+  for (int q = 0; q < 2; ++q) {
+    const uint32_t p = ps[q], psi = roots[q], psi_inv = rns::invm(psi, p);
+    const uint32_t inv1024 = rns::invm(1024, p);
+    for (int k2 = 0; k2 < 16; ++k2)
+      for (int n1 = 0; n1 < 64; ++n1) {
+        const uint64_t e = uint64_t(2 * k2 + 1) * n1;
+        const uint32_t wf = rns::powm(psi, e, p);
+        const uint32_t wi = rns::mulm(rns::powm(psi_inv, e, p), inv1024, p);
+        uint4 &F = out[k2 * 64 + n1], &I = out[1024 + k2 * 64 + n1];
+        (q == 0 ? F.x : F.z) = wf;
+        (q == 0 ? F.y : F.w) = rns::shoup_of(wf, p);
+        (q == 0 ? I.x : I.z) = wi;
+        (q == 0 ? I.y : I.w) = rns::shoup_of(wi, p);
+      }
   }
-  const uint64_t psi_inv = powmod(psi, kP - 2);
-  const uint64_t inv1024 = powmod(1024, kP - 2);
-  for (int k2 = 0; k2 < 16; ++k2)
-    for (int n1 = 0; n1 < 64; ++n1) {
-      const uint64_t e = uint64_t(2 * k2 + 1) * n1;
-      out[k2 * 64 + n1] = powmod(psi, e);
-      out[1024 + k2 * 64 + n1] = mulmod(powmod(psi_inv, e), inv1024);
-    }
 }
 
 }  // namespace ce
@@ -236,12 +220,12 @@ extern "C" ce_status ce_create(ce_ctx **out, int device, uint64_t hbm_budget_byt
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
   ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : uint64_t(free_b) / 10 * 9;
-  std::vector<uint64_t> tw(2048);
+  std::vector<uint4> tw(kTwistEntries);
   transform_tables(tw.data());
-  e = cudaMalloc(&ctx->tw, 2048 * sizeof(uint64_t));
+  e = cudaMalloc(&ctx->tw, kTwistEntries * sizeof(uint4));
   if (e == cudaSuccess) e = cudaMalloc(&ctx->err, sizeof(int));
   if (e == cudaSuccess)
-    e = cudaMemcpy(ctx->tw, tw.data(), 2048 * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(ctx->tw, tw.data(), kTwistEntries * sizeof(uint4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(ctx->err, 0, sizeof(int));
   if (e != cudaSuccess) {
     ce_destroy(ctx);

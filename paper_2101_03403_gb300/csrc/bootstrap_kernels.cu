@@ -11,9 +11,8 @@
 #include <cstdint>
 
 #include "ce_internal.h"
-#include "gl_field.cuh"
 #include "launch.h"
-#include "ntt_pair.cuh"
+#include "rns_ntt.cuh"
 
 namespace ce {
 
@@ -160,7 +159,7 @@ template <int G, int NSLOT>
 struct BrSmem {
   static constexpr size_t kRing = size_t(NSLOT) * kChunkWords * 8;
   static constexpr size_t kAcc = 2 * kRingN * 4;                 // per gate
-  static constexpr size_t kBuf = size_t(ntt::kBufWords) * 8;     // per gate
+  static constexpr size_t kBuf = size_t(rns::kBufWords) * 8;     // per gate
   static constexpr size_t kGate = kAcc + kBuf;
   static constexpr size_t kBars = 64;
   static constexpr size_t kTotal = kRing + G * kGate + kBars + 64;
@@ -170,17 +169,17 @@ template <int G, int NSLOT>
 __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
     const uint64_t *__restrict__ bsk, const uint64_t *const *__restrict__ grp_bsk,
     const uint16_t *__restrict__ abar, uint32_t *__restrict__ acc_out, int n_jobs,
-    const uint64_t *__restrict__ tw, int *__restrict__ err) {
+    const uint4 *__restrict__ tw, int *__restrict__ err) {
   using L = BrSmem<G, NSLOT>;
   extern __shared__ __align__(128) uint8_t smem[];
   uint64_t *ring = reinterpret_cast<uint64_t *>(smem);
   const int g = threadIdx.x >> 7, t = threadIdx.x & 127, lane = threadIdx.x & 31;
   uint32_t *acc = reinterpret_cast<uint32_t *>(smem + L::kRing + g * L::kGate);
-  uint64_t *buf = reinterpret_cast<uint64_t *>(smem + L::kRing + g * L::kGate + L::kAcc);
+  uint2 *buf = reinterpret_cast<uint2 *>(smem + L::kRing + g * L::kGate + L::kAcc);
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::kRing + G * L::kGate);
   uint32_t *count = reinterpret_cast<uint32_t *>(full + NSLOT);
   volatile int *abort = reinterpret_cast<volatile int *>(count + NSLOT);
-  const uint64_t *tw_fwd = tw, *tw_inv = tw + 1024;
+  const uint4 *tw_fwd = tw, *tw_inv = tw + 1024;
   constexpr int kChunksPerGate = kLweN * kGadgetL;  // 1500
   constexpr int kWarps = 4 * G;
   constexpr int kThreads = 128 * G;
@@ -228,7 +227,7 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
         acc[kRingN + j] = hi ? kMuEighth : 0u - kMuEighth;
       }
     }
-    ntt::named_bar(1, kThreads);
+    rns::named_bar(1, kThreads);
 
     for (int i = 0; i < kLweN; ++i) {
       // Every gate of the block runs every step in lockstep (block-wide
@@ -237,7 +236,7 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
       // step adds exactly zero.
       const int rot = active ? __ldg(ab + i) : 0;
       uint32_t w[16];
-      uint64_t X[2][8];
+      uint32_t X[2][2][8];  // [prime][output polynomial][position]
       {
         // w = X^rot ACC_P - ACC_P + decomposition offset, at n = n1 + 64 n2.
         const uint32_t *src = acc + P * kRingN;
@@ -252,38 +251,37 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
           w[n2] = r - src[n] + kDecompOffset;
         }
 #pragma unroll
-        for (int o = 0; o < 2; ++o)
+        for (int q = 0; q < 2; ++q)
 #pragma unroll
-          for (int d = 0; d < 8; ++d) X[o][d] = 0;
+          for (int o = 0; o < 2; ++o)
+#pragma unroll
+            for (int d = 0; d < 8; ++d) X[q][o][d] = 0;
       }
 #pragma unroll 1
       for (int pz = 0; pz < kGadgetL; ++pz, ++chunk) {
         const int slot = chunk % NSLOT;
-        uint64_t v[16], Y[2][8];
+        uint32_t v[2][16], Y[2][2][8];
         const int sh = 22 - 10 * pz;
 #pragma unroll
         for (int n2 = 0; n2 < 16; ++n2) {
-          const int32_t dgt = int32_t((w[n2] >> sh) & 1023u) - 512;
-          // Negacyclic pre-twist psi^(64 n2) = 2^(6 n2) applied to the small
-          // digit directly: |d| 2^(6 n2) < 2^63 for n2 <= 9 needs no reduction.
-          if (n2 <= 9) {
-            const uint64_t mag = static_cast<uint64_t>(dgt < 0 ? -dgt : dgt) << (6 * n2);
-            v[n2] = dgt < 0 ? gl::kP - mag : mag;
-          } else {
-            v[n2] = gl::mul_pow2(gl::from_i32(dgt), 6 * n2);
-          }
+          // digit + 512 in [0, 1024); digit + p lies in (0, 2p).
+          const uint32_t u = (w[n2] >> sh) & 1023u;
+          v[0][n2] = rns::pretwist<0>(u + (rns::P<0>() - 512u), n2);
+          v[1][n2] = rns::pretwist<1>(u + (rns::P<1>() - 512u), n2);
         }
-        ntt::forward_pretwisted(v, Y, buf, t, 1, kThreads, tw_fwd);
+        rns::forward(v, Y, buf, t, 1, kThreads, tw_fwd);
         wait_slot(smem_u32(full + slot), uint32_t(chunk / NSLOT) & 1u, abort, err);
-        // X[o] += Y[0] * key(c=0, p, o) + Y[1] * key(c=1, p, o)
-        const uint64_t *key = ring + size_t(slot) * kChunkWords + t;
+        // X[o] += Y[0] * key(c=0, p, o) + Y[1] * key(c=1, p, o), per prime;
+        // key words are (k mod p0, k mod p1) in Montgomery form.
+        const uint2 *key = reinterpret_cast<const uint2 *>(ring) + size_t(slot) * kChunkWords + t;
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
 #pragma unroll
           for (int o = 0; o < 2; ++o) {
-            const uint64_t k0 = key[((0 * 2 + o) * 8 + d) * 128];
-            const uint64_t k1 = key[((1 * 2 + o) * 8 + d) * 128];
-            X[o][d] = gl::mac2(X[o][d], Y[0][d], k0, Y[1][d], k1);
+            const uint2 k0 = key[((0 * 2 + o) * 8 + d) * 128];
+            const uint2 k1 = key[((1 * 2 + o) * 8 + d) * 128];
+            X[0][o][d] += rns::redc<0>(uint64_t(Y[0][0][d]) * k0.x + uint64_t(Y[0][1][d]) * k1.x);
+            X[1][o][d] += rns::redc<1>(uint64_t(Y[1][0][d]) * k0.y + uint64_t(Y[1][1][d]) * k1.y);
           }
         }
         // Release the slot; the last warp out refills it with chunk + NSLOT.
@@ -302,19 +300,27 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
         }
       }
       {
-        uint64_t v[16];
-        ntt::inverse(X, v, buf, t, 1, kThreads, tw_inv);
+        // Three levels of [0, 2p) terms: below 6p; the inverse takes [0, 4p).
+#pragma unroll
+        for (int o = 0; o < 2; ++o)
+#pragma unroll
+          for (int d = 0; d < 8; ++d) {
+            X[0][o][d] = rns::fold<0, 4>(X[0][o][d]);
+            X[1][o][d] = rns::fold<1, 4>(X[1][o][d]);
+          }
+        uint32_t v[2][16];
+        rns::inverse(X, v, buf, t, 1, kThreads, tw_inv);
         uint32_t *dst = acc + P * kRingN + n1;
 #pragma unroll
-        for (int n2 = 0; n2 < 16; ++n2) dst[64 * n2] += gl::lift32(v[n2]);
+        for (int n2 = 0; n2 < 16; ++n2) dst[64 * n2] += rns::lift32(v[0][n2], v[1][n2]);
       }
-      ntt::named_bar(1, kThreads);
+      rns::named_bar(1, kThreads);
     }
     if (active) {
       uint32_t *out = acc_out + size_t(job) * 2 * kRingN;
       for (int j = t; j < 2 * kRingN; j += 128) out[j] = acc[j];
     }
-    ntt::named_bar(1, kThreads);
+    rns::named_bar(1, kThreads);
   }
 }
 
@@ -329,7 +335,7 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
 struct WideSmem {
   static constexpr size_t kSlots = size_t(3) * kChunkWords * 8;
   static constexpr size_t kAcc = 2 * kRingN * 4;
-  static constexpr size_t kBufs = size_t(3) * ntt::kBufWords * 8;
+  static constexpr size_t kBufs = size_t(3) * rns::kBufWords * 8;
   static constexpr size_t kXch = size_t(2) * 2 * 8 * 128 * 8;
   static constexpr size_t kTotal = kSlots + kAcc + kBufs + kXch + 64;
 };
@@ -337,19 +343,19 @@ struct WideSmem {
 __global__ void __launch_bounds__(384, 1) blind_rotate_wide_kernel(
     const uint64_t *__restrict__ bsk, const uint64_t *const *__restrict__ gate_bsk,
     const uint16_t *__restrict__ abar, uint32_t *__restrict__ acc_out, int n_jobs,
-    const uint64_t *__restrict__ tw, int *__restrict__ err) {
+    const uint4 *__restrict__ tw, int *__restrict__ err) {
   using L = WideSmem;
   extern __shared__ __align__(128) uint8_t smem[];
   uint64_t *slots = reinterpret_cast<uint64_t *>(smem);
   uint32_t *acc = reinterpret_cast<uint32_t *>(smem + L::kSlots);
-  uint64_t *bufs = reinterpret_cast<uint64_t *>(smem + L::kSlots + L::kAcc);
-  uint64_t *xch = reinterpret_cast<uint64_t *>(smem + L::kSlots + L::kAcc + L::kBufs);
+  uint2 *bufs = reinterpret_cast<uint2 *>(smem + L::kSlots + L::kAcc);
+  uint2 *xch = reinterpret_cast<uint2 *>(smem + L::kSlots + L::kAcc + L::kBufs);
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::kSlots + L::kAcc + L::kBufs + L::kXch);
   volatile int *abort = reinterpret_cast<volatile int *>(full + 3);
   const int g = threadIdx.x >> 7, t = threadIdx.x & 127;
-  uint64_t *buf = bufs + g * ntt::kBufWords;
+  uint2 *buf = bufs + g * rns::kBufWords;
   uint64_t *slot = slots + size_t(g) * kChunkWords;
-  const uint64_t *tw_fwd = tw, *tw_inv = tw + 1024;
+  const uint4 *tw_fwd = tw, *tw_inv = tw + 1024;
   const int my_gates = int(blockIdx.x) < n_jobs ? (n_jobs - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
   const int total = my_gates * kLweN;  // chunks per group
   auto chunk_src = [&](int c) {
@@ -382,7 +388,7 @@ __global__ void __launch_bounds__(384, 1) blind_rotate_wide_kernel(
     __syncthreads();
     for (int i = 0; i < kLweN; ++i, ++c) {
       const int rot = __ldg(ab + i);
-      uint64_t v[16], Y[2][8];
+      uint32_t v[2][16], Y[2][2][8];
       {
         const uint32_t *src = acc + P * kRingN;
         const int kk = rot & (kRingN - 1);
@@ -395,48 +401,51 @@ __global__ void __launch_bounds__(384, 1) blind_rotate_wide_kernel(
           uint32_t r = sidx >= 0 ? src[sidx] : 0u - src[sidx + kRingN];
           r = (r ^ flip) - flip;
           const uint32_t wv = r - src[n] + kDecompOffset;
-          const int32_t dgt = int32_t((wv >> sh) & 1023u) - 512;
-          if (n2 <= 9) {
-            const uint64_t mag = static_cast<uint64_t>(dgt < 0 ? -dgt : dgt) << (6 * n2);
-            v[n2] = dgt < 0 ? gl::kP - mag : mag;
-          } else {
-            v[n2] = gl::mul_pow2(gl::from_i32(dgt), 6 * n2);
-          }
+          const uint32_t u = (wv >> sh) & 1023u;  // digit + 512
+          v[0][n2] = rns::pretwist<0>(u + (rns::P<0>() - 512u), n2);
+          v[1][n2] = rns::pretwist<1>(u + (rns::P<1>() - 512u), n2);
         }
       }
-      ntt::forward_pretwisted(v, Y, buf, t, 1 + g, 128, tw_fwd);
+      rns::forward(v, Y, buf, t, 1 + g, 128, tw_fwd);
       wait_slot(smem_u32(full + g), uint32_t(c) & 1u, abort, err);
-      uint64_t X[2][8];
+      uint32_t X[2][2][8];  // this level's products, each in [0, 2p)
       {
-        const uint64_t *key = slot + t;
+        const uint2 *key = reinterpret_cast<const uint2 *>(slot) + t;
 #pragma unroll
         for (int d = 0; d < 8; ++d)
 #pragma unroll
-          for (int o = 0; o < 2; ++o)
-            X[o][d] = gl::mul2_add(Y[0][d], key[((0 * 2 + o) * 8 + d) * 128], Y[1][d],
-                                   key[((1 * 2 + o) * 8 + d) * 128]);
+          for (int o = 0; o < 2; ++o) {
+            const uint2 k0 = key[((0 * 2 + o) * 8 + d) * 128];
+            const uint2 k1 = key[((1 * 2 + o) * 8 + d) * 128];
+            X[0][o][d] = rns::redc<0>(uint64_t(Y[0][0][d]) * k0.x + uint64_t(Y[0][1][d]) * k1.x);
+            X[1][o][d] = rns::redc<1>(uint64_t(Y[1][0][d]) * k0.y + uint64_t(Y[1][1][d]) * k1.y);
+          }
       }
-      ntt::named_bar(1 + g, 128);  // the group is done with its slot
+      rns::named_bar(1 + g, 128);  // the group is done with its slot
       if (t == 0 && c + 1 < total && !*abort) issue_chunk(slot, smem_u32(full + g), chunk_src(c + 1));
       if (g > 0) {
-        uint64_t *x = xch + size_t(g - 1) * 2 * 8 * 128 + t;
+        uint2 *x = xch + size_t(g - 1) * 2 * 8 * 128 + t;
 #pragma unroll
         for (int o = 0; o < 2; ++o)
 #pragma unroll
-          for (int d = 0; d < 8; ++d) x[(o * 8 + d) * 128] = X[o][d];
+          for (int d = 0; d < 8; ++d) x[(o * 8 + d) * 128] = make_uint2(X[0][o][d], X[1][o][d]);
       }
       __syncthreads();
       if (g == 0) {
-        const uint64_t *x1 = xch + t, *x2 = xch + 2 * 8 * 128 + t;
+        const uint2 *x1 = xch + t, *x2 = xch + 2 * 8 * 128 + t;
 #pragma unroll
         for (int o = 0; o < 2; ++o)
 #pragma unroll
-          for (int d = 0; d < 8; ++d)
-            X[o][d] = gl::add(X[o][d], gl::add(x1[(o * 8 + d) * 128], x2[(o * 8 + d) * 128]));
-        ntt::inverse(X, v, buf, t, 1, 128, tw_inv);
+          for (int d = 0; d < 8; ++d) {
+            // three [0, 2p) terms: below 6p; the inverse takes [0, 4p)
+            const uint2 a1 = x1[(o * 8 + d) * 128], a2 = x2[(o * 8 + d) * 128];
+            X[0][o][d] = rns::fold<0, 4>(X[0][o][d] + a1.x + a2.x);
+            X[1][o][d] = rns::fold<1, 4>(X[1][o][d] + a1.y + a2.y);
+          }
+        rns::inverse(X, v, buf, t, 1, 128, tw_inv);
         uint32_t *dst = acc + P * kRingN + n1;
 #pragma unroll
-        for (int n2 = 0; n2 < 16; ++n2) dst[64 * n2] += gl::lift32(v[n2]);
+        for (int n2 = 0; n2 < 16; ++n2) dst[64 * n2] += rns::lift32(v[0][n2], v[1][n2]);
       }
       __syncthreads();
     }
@@ -552,25 +561,34 @@ __global__ void zero_slots_kernel(const GateOut *__restrict__ outs, uint32_t *__
 
 // --------------------------------------------------------- key to transform ---
 // Block (i, p): transforms the four polynomials (TRGSW half c, component o)
-// of bootstrapping-key rows r = c*3 + p of key bit i and stores them in the
-// [i][p][c*2+o][d][thread] order the blind rotation reads.
+// of bootstrapping-key rows r = c*3 + p of key bit i (coefficients lifted to
+// [-2^31, 2^31)) and stores them, reduced and in Montgomery form, in the
+// [i][p][c*2+o][d][thread] order the blind rotation reads: one 64-bit word
+// per position holding the residues (mod p0, mod p1).
 __global__ void __launch_bounds__(128) bsk_to_transform_kernel(const uint32_t *__restrict__ bsk,
-                                                               uint64_t *__restrict__ out,
-                                                               const uint64_t *__restrict__ tw) {
-  __shared__ uint64_t buf[ntt::kBufWords];
+                                                               uint2 *__restrict__ out,
+                                                               const uint4 *__restrict__ tw) {
+  __shared__ uint2 buf[rns::kBufWords];
   const int i = blockIdx.x / kGadgetL, pz = blockIdx.x % kGadgetL, t = threadIdx.x;
   const int P = t >> 6, n1 = t & 63;
   for (int c = 0; c < 2; ++c) {
     const uint32_t *row = bsk + ((size_t(i) * 2 * kGadgetL + c * kGadgetL + pz) * 2 + P) * kRingN;
-    uint64_t v[16], X[2][8];
+    uint32_t v[2][16], X[2][2][8];
 #pragma unroll
-    for (int n2 = 0; n2 < 16; ++n2) v[n2] = row[n1 + 64 * n2];
-    ntt::forward(v, X, buf, t, 1, 128, tw);
-    uint64_t *dst = out + size_t(blockIdx.x) * kChunkWords;
+    for (int n2 = 0; n2 < 16; ++n2) {
+      const int32_t k = int32_t(row[n1 + 64 * n2]);
+      v[0][n2] = rns::pretwist<0>(rns::from_i32<0>(k), n2);
+      v[1][n2] = rns::pretwist<1>(rns::from_i32<1>(k), n2);
+    }
+    rns::forward(v, X, buf, t, 1, 128, tw);
+    uint2 *dst = out + size_t(blockIdx.x) * kChunkWords;
 #pragma unroll
     for (int o = 0; o < 2; ++o)
 #pragma unroll
-      for (int d = 0; d < 8; ++d) dst[((c * 2 + o) * 8 + d) * 128 + t] = X[o][d];
+      for (int d = 0; d < 8; ++d)
+        dst[((c * 2 + o) * 8 + d) * 128 + t] =
+            make_uint2(rns::fold<0, 1>(rns::to_mont<0>(X[0][o][d])),
+                       rns::fold<1, 1>(rns::to_mont<1>(X[1][o][d])));
   }
 }
 
@@ -579,33 +597,45 @@ __global__ void __launch_bounds__(128) bsk_to_transform_kernel(const uint32_t *_
 __global__ void __launch_bounds__(128) negacyclic_mul_kernel(const int16_t *__restrict__ dg,
                                                              const uint32_t *__restrict__ k,
                                                              uint32_t *__restrict__ out, int n,
-                                                             const uint64_t *__restrict__ tw) {
-  __shared__ uint64_t buf[ntt::kBufWords];
+                                                             const uint4 *__restrict__ tw) {
+  __shared__ uint2 buf[rns::kBufWords];
   const int t = threadIdx.x, P = t >> 6, n1 = t & 63;
   const int prod = 2 * blockIdx.x + P;
   const bool live = prod < n;
-  uint64_t v[16], XD[2][8], XK[2][8];
+  uint32_t v[2][16], XD[2][2][8], XK[2][2][8];
 #pragma unroll
-  for (int n2 = 0; n2 < 16; ++n2)
-    v[n2] = live ? gl::from_i32(dg[size_t(prod) * kRingN + n1 + 64 * n2]) : 0;
-  ntt::forward(v, XD, buf, t, 1, 128, tw);
+  for (int n2 = 0; n2 < 16; ++n2) {
+    const int32_t x = live ? dg[size_t(prod) * kRingN + n1 + 64 * n2] : 0;
+    v[0][n2] = rns::pretwist<0>(rns::from_i32<0>(x), n2);
+    v[1][n2] = rns::pretwist<1>(rns::from_i32<1>(x), n2);
+  }
+  rns::forward(v, XD, buf, t, 1, 128, tw);
 #pragma unroll
-  for (int n2 = 0; n2 < 16; ++n2) v[n2] = live ? k[size_t(prod) * kRingN + n1 + 64 * n2] : 0;
-  ntt::forward(v, XK, buf, t, 1, 128, tw);
+  for (int n2 = 0; n2 < 16; ++n2) {
+    const int32_t x = live ? int32_t(k[size_t(prod) * kRingN + n1 + 64 * n2]) : 0;
+    v[0][n2] = rns::pretwist<0>(rns::from_i32<0>(x), n2);
+    v[1][n2] = rns::pretwist<1>(rns::from_i32<1>(x), n2);
+  }
+  rns::forward(v, XK, buf, t, 1, 128, tw);
+  // XD * XK = redc(XD * mont(XK)); mont(XK) < 2p keeps the product below 2^59.
 #pragma unroll
   for (int q = 0; q < 2; ++q)
 #pragma unroll
-    for (int d = 0; d < 8; ++d) XD[q][d] = gl::mul(XD[q][d], XK[q][d]);
-  ntt::inverse(XD, v, buf, t, 1, 128, tw + 1024);
+    for (int d = 0; d < 8; ++d) {
+      XD[0][q][d] = rns::redc<0>(uint64_t(XD[0][q][d]) * rns::to_mont<0>(XK[0][q][d]));
+      XD[1][q][d] = rns::redc<1>(uint64_t(XD[1][q][d]) * rns::to_mont<1>(XK[1][q][d]));
+    }
+  rns::inverse(XD, v, buf, t, 1, 128, tw + 1024);
   if (live) {
 #pragma unroll
-    for (int n2 = 0; n2 < 16; ++n2) out[size_t(prod) * kRingN + n1 + 64 * n2] = gl::lift32(v[n2]);
+    for (int n2 = 0; n2 < 16; ++n2)
+      out[size_t(prod) * kRingN + n1 + 64 * n2] = rns::lift32(v[0][n2], v[1][n2]);
   }
 }
 
 template <int G, int NSLOT>
 cudaError_t launch_br(const uint64_t *bsk, const uint64_t *const *grp_bsk, const uint16_t *abar,
-                      uint32_t *acc, int n, const uint64_t *tw, int *err, int blocks,
+                      uint32_t *acc, int n, const uint4 *tw, int *err, int blocks,
                       cudaStream_t st) {
   using L = BrSmem<G, NSLOT>;
   auto kern = blind_rotate_kernel<G, NSLOT>;
@@ -636,7 +666,7 @@ cudaError_t launch_lincomb_modswitch(const uint8_t *ops, const uint32_t *a, cons
 }
 
 cudaError_t launch_blind_rotate(const uint64_t *bsk, const uint16_t *abar, uint32_t *acc,
-                                int n_jobs, const uint64_t *tw, int *err, int gates_per_block,
+                                int n_jobs, const uint4 *tw, int *err, int gates_per_block,
                                 int blocks, cudaStream_t st, const uint64_t *const *grp_bsk) {
   if (n_jobs <= 0) return cudaSuccess;
   switch (gates_per_block) {
@@ -700,14 +730,15 @@ cudaError_t launch_zero_slots(const GateOut *outs, uint32_t *arena, int n_out, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_bsk_to_transform(const uint32_t *bsk, uint64_t *out, const uint64_t *tw,
+cudaError_t launch_bsk_to_transform(const uint32_t *bsk, uint64_t *out, const uint4 *tw,
                                     cudaStream_t st) {
-  bsk_to_transform_kernel<<<kLweN * kGadgetL, 128, 0, st>>>(bsk, out, tw);
+  bsk_to_transform_kernel<<<kLweN * kGadgetL, 128, 0, st>>>(bsk, reinterpret_cast<uint2 *>(out),
+                                                             tw);
   return cudaGetLastError();
 }
 
 cudaError_t launch_negacyclic_mul(const int16_t *d, const uint32_t *k, uint32_t *out, int n,
-                                  const uint64_t *tw, cudaStream_t st) {
+                                  const uint4 *tw, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   negacyclic_mul_kernel<<<(n + 1) / 2, 128, 0, st>>>(d, k, out, n, tw);
   return cudaGetLastError();

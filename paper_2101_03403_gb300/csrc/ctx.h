@@ -31,7 +31,7 @@ struct ce_ctx {
   int sms = 0;
   uint64_t budget = 0, used = 0;
   std::vector<ce::Client> clients;
-  uint64_t *tw = nullptr;
+  uint4 *tw = nullptr;
   int *err = nullptr;
   uint16_t *abar = nullptr;
   uint32_t *acc = nullptr;

@@ -15,7 +15,7 @@ cudaError_t launch_lincomb_modswitch(const uint8_t *ops, const uint32_t *a, cons
                                      int *err, cudaStream_t st);
 // grp_bsk (optional): per gate-group key (group g = gates [g*G, g*G+G)).
 cudaError_t launch_blind_rotate(const uint64_t *bsk, const uint16_t *abar, uint32_t *acc,
-                                int n_jobs, const uint64_t *tw, int *err, int gates_per_block,
+                                int n_jobs, const uint4 *tw, int *err, int gates_per_block,
                                 int blocks, cudaStream_t st,
                                 const uint64_t *const *grp_bsk = nullptr);
 size_t blind_rotate_smem_bytes(int gates_per_block);
@@ -42,23 +42,26 @@ cudaError_t launch_extract_keyswitch_ex(const uint32_t *acc, const uint32_t *ksk
                                         uint32_t *out, int n_out, int mode, int tile, int jsplit,
                                         cudaStream_t st);
 cudaError_t launch_zero_slots(const GateOut *outs, uint32_t *arena, int n_out, cudaStream_t st);
-cudaError_t launch_bsk_to_transform(const uint32_t *bsk, uint64_t *out, const uint64_t *tw,
+cudaError_t launch_bsk_to_transform(const uint32_t *bsk, uint64_t *out, const uint4 *tw,
                                     cudaStream_t st);
 cudaError_t launch_negacyclic_mul(const int16_t *d, const uint32_t *k, uint32_t *out, int n,
-                                  const uint64_t *tw, cudaStream_t st);
+                                  const uint4 *tw, cudaStream_t st);
 
 struct GatePathResources {
   const uint64_t *bsk;   // transform-domain bootstrapping key of the client
   const uint32_t *ksk;   // device key-switching key of the client
-  const uint64_t *tw;    // twist tables
+  const uint4 *tw;       // twist tables
   int *err;              // device error flag of the context
   int device;
   cudaStream_t stream;
 };
 
-// Forward twist table psi^((2 k2 + 1) n1) at [k2 * 64 + n1] and the inverse
-// table psi^(-(2 k2 + 1) n1) / 1024 at [1024 + k2 * 64 + n1].
-void transform_tables(uint64_t *host_out /* 2048 words */);
+// Twist tables of the two-prime transform, one uint4 {w0, w0', w1, w1'} per
+// entry (residue mod p_q and its Shoup quotient): forward psi_q^((2 k2 + 1) n1)
+// at [k2 * 64 + n1], inverse psi_q^(-(2 k2 + 1) n1) / 1024 at
+// [1024 + k2 * 64 + n1].
+constexpr size_t kTwistEntries = 2048;
+void transform_tables(uint4 *host_out /* kTwistEntries */);
 
 }  // namespace ce
 

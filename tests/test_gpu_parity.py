@@ -15,10 +15,13 @@ def test_negacyclic_mul_matches_oracle(ce, ctx, O):
     rng = np.random.default_rng(11)
     n = 37  # odd: the last block carries one product
     d = rng.integers(-512, 512, (n, 1024)).astype(np.int16)
-    d[3] = rng.integers(-2 ** 15, 2 ** 15, 1024)          # full int16 range
-    d[4] = -2 ** 15
+    d[3] = rng.integers(-2 ** 13, 2 ** 13 + 1, 1024)      # full documented range
+    d[4] = -2 ** 13
+    d[6] = 2 ** 13
     k = rng.integers(0, 2 ** 32, (n, 1024), dtype=np.uint64).astype(np.uint32)
     k[5] = 0xFFFFFFFF
+    k[4] = 0x80000000      # every term +2^44: the exact sum is 2^54, the bound
+    k[6] = 0x80000000      # every term -2^44: -2^54
     out = torch.empty((n, 1024), dtype=torch.int32, device="cuda")
     ce.ce_negacyclic_mul_device(c, to_dev(d), to_dev(k.view(np.int32)), out, n)
     torch.cuda.synchronize()

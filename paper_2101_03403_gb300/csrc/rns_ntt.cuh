@@ -57,24 +57,43 @@ RNS_TD Tw root(int e) {
   return RNS_U.r8[DIR][Q][e];
 }
 
+#ifdef RNS_RANGE_CHECK  // host builds of this header may check every lazy bound
+#define RNS_EXPECT(x, bound) rns_range_check((x) < (bound))
+#else
+#define RNS_EXPECT(x, bound) ((void)0)
+#endif
+
 // In-register transform V[k] = sum_n v[n] w^(n k), w = psi^(+-2048/M)
-// (DIR 0: +, 1: -), values in [0, 4p) throughout.  Radix-2 decimation in
-// frequency; the bit-reversed output order is undone by renaming registers.
-template <int M, int DIR, int Q>
+// (DIR 0: +, 1: -).  Radix-2 decimation in frequency; the bit-reversed
+// output order is undone by renaming registers.  Inputs lie in [0, 4p), or
+// in [0, 2p) when IN2P (then the first stage needs no reduction); outputs
+// lie in [0, 4p), except outputs k of the last stage whose bit in FOLD is
+// clear: those are left in [0, 8p) for a consumer that multiplies them
+// (a Shoup product or a Montgomery sum accepts any 32-bit value).
+template <int M, int DIR, int Q, bool IN2P = false, unsigned FOLD = 0xFFFFu>
 RNS_TD void dft(uint32_t (&v)[M]) {
   constexpr int LOG = ilog2(M);
 #pragma unroll
   for (int st = 0; st < LOG; ++st) {
     const int len = M >> (st + 1);
+    const bool first = IN2P && st == 0, last = st == LOG - 1;
+    const uint32_t off = (first ? 2u : 4u) * P<Q>();
 #pragma unroll
     for (int j0 = 0; j0 < M; j0 += 2 * len) {
 #pragma unroll
       for (int i = 0; i < len; ++i) {
         const int e = i * (M / (2 * len));
+        uint32_t &a = v[j0 + i], &b = v[j0 + i + len];
+        RNS_EXPECT(a, (first ? 2u : 4u) * P<Q>());
+        RNS_EXPECT(b, (first ? 2u : 4u) * P<Q>());
+        const uint32_t s = a + b, d = a + off - b;
+        const bool fold_s = !first && (!last || ((FOLD >> bitrev(j0 + i, LOG)) & 1u));
+        const bool fold_d = !first && (!last || ((FOLD >> bitrev(j0 + i + len, LOG)) & 1u));
+        a = fold_s ? fold<Q, 4>(s) : s;
         if (e == 0)
-          bfly1<Q>(v[j0 + i], v[j0 + i + len]);
+          b = fold_d ? fold<Q, 4>(d) : d;
         else
-          bfly<Q>(v[j0 + i], v[j0 + i + len], root<M, DIR, Q>(e));
+          b = shoup<Q>(d, root<M, DIR, Q>(e));
       }
     }
   }
@@ -106,8 +125,8 @@ RNS_TD uint32_t pretwist(uint32_t u, int n2) {
 // mod p_q, pre-twisted.
 RNS_TD void fwd_phase_a(uint32_t (&v)[2][16], uint2 *buf, int t, const uint4 *tw_fwd) {
   const int Pp = t >> 6, n1 = t & 63;
-  dft<16, 0, 0>(v[0]);
-  dft<16, 0, 1>(v[1]);
+  dft<16, 0, 0, true, 0u>(v[0]);  // every output is twisted
+  dft<16, 0, 1, true, 0u>(v[1]);
   uint2 *col = buf + Pp * 16 * kRow + n1;
 #pragma unroll
   for (int k2 = 0; k2 < 16; ++k2) {
@@ -131,8 +150,8 @@ RNS_TD void fwd_phase_c1(uint2 *buf, int wg, int lane) {
       u0[b] = x.x;
       u1[b] = x.y;
     }
-    dft<8, 0, 0>(u0);
-    dft<8, 0, 1>(u1);
+    dft<8, 0, 0, true, 1u>(u0);  // outputs c >= 1 are multiplied below
+    dft<8, 0, 1, true, 1u>(u1);
     row[a] = make_uint2(u0[0], u1[0]);
 #pragma unroll
     for (int c = 1; c < 8; ++c)
@@ -141,7 +160,8 @@ RNS_TD void fwd_phase_c1(uint2 *buf, int wg, int lane) {
   }
 }
 
-// Phase C2: thread (k2, c) = (t & 15, t >> 4), both polynomials.
+// Phase C2: thread (k2, c) = (t & 15, t >> 4), both polynomials.  Outputs
+// lie in [0, 8p) (products accept them).
 RNS_TD void fwd_phase_c2(uint32_t (&X)[2][2][8], const uint2 *buf, int t) {
   const int k2 = t & 15, c = t >> 4;
 #pragma unroll
@@ -153,8 +173,8 @@ RNS_TD void fwd_phase_c2(uint32_t (&X)[2][2][8], const uint2 *buf, int t) {
       X[0][Pp][a] = x.x;
       X[1][Pp][a] = x.y;
     }
-    dft<8, 0, 0>(X[0][Pp]);
-    dft<8, 0, 1>(X[1][Pp]);
+    dft<8, 0, 0, false, 0u>(X[0][Pp]);  // outputs feed products: [0, 8p)
+    dft<8, 0, 1, false, 0u>(X[1][Pp]);
   }
 }
 
@@ -190,8 +210,8 @@ RNS_TD void inv_phase_c1(uint2 *buf, int wg, int lane) {
       u0[c] = shoup<0>(x.x, RNS_U.c1[1][0][a * 8 + c]);
       u1[c] = shoup<1>(x.y, RNS_U.c1[1][1][a * 8 + c]);
     }
-    dft<8, 1, 0>(u0);
-    dft<8, 1, 1>(u1);
+    dft<8, 1, 0, false, 0u>(u0);  // phase A multiplies every output
+    dft<8, 1, 1, false, 0u>(u1);
 #pragma unroll
     for (int b = 0; b < 8; ++b) row[a + 8 * b] = make_uint2(u0[b], u1[b]);
   }
@@ -208,8 +228,8 @@ RNS_TD void inv_phase_a(uint32_t (&v)[2][16], const uint2 *buf, int t, const uin
     v[0][k2] = shoup<0>(x.x, T.x, T.y);
     v[1][k2] = shoup<1>(x.y, T.z, T.w);
   }
-  dft<16, 1, 0>(v[0]);
-  dft<16, 1, 1>(v[1]);
+  dft<16, 1, 0, true, 1u>(v[0]);  // outputs n2 >= 1 are multiplied below
+  dft<16, 1, 1, true, 1u>(v[1]);
 #pragma unroll
   for (int n2 = 1; n2 < 16; ++n2) {
     v[0][n2] = shoup<0>(v[0][n2], RNS_U.pre[1][0][n2]);
@@ -226,7 +246,8 @@ __device__ __forceinline__ void named_bar(int id, int count) {
 }
 
 // Forward transform of two polynomials; v holds this thread's pre-twisted
-// phase-A inputs (clobbered); X receives the eight positions of each.
+// phase-A inputs in [0, 2p) (clobbered); X receives the eight positions of
+// each, in [0, 8p).
 __device__ __forceinline__ void forward(uint32_t (&v)[2][16], uint32_t (&X)[2][2][8], uint2 *buf,
                                         int t, int bar, int nthr, const uint4 *tw_fwd) {
   named_bar(bar, nthr);  // the buffer is free

@@ -96,6 +96,9 @@ __global__ void __launch_bounds__(512) lincomb_gather_kernel(const GateJob *__re
 // domain rows of CMux step i, gadget level p (4 polynomials, 32 KB) arrive by
 // bulk asynchronous copy into a ring of NSLOT shared-memory slots and are
 // used by all G gates.  The last warp to finish with a slot refills it.
+// Each gate's group synchronises only itself (named barrier 1 + g), so the
+// groups drift within the ring's slack and their multiply-heavy and
+// add-heavy phases overlap on the SM's two integer pipes.
 //
 // Per gate and step i (a CMux controlled by key bit s_i): D = X^abar_i ACC -
 // ACC; for p = 1..3: forward-transform digit p of both halves of D, multiply
@@ -182,7 +185,6 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
   const uint4 *tw_fwd = tw, *tw_inv = tw + 1024;
   constexpr int kChunksPerGate = kLweN * kGadgetL;  // 1500
   constexpr int kWarps = 4 * G;
-  constexpr int kThreads = 128 * G;
 
   const int n_groups = (n_jobs + G - 1) / G;
   const int my_groups =
@@ -227,13 +229,11 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
         acc[kRingN + j] = hi ? kMuEighth : 0u - kMuEighth;
       }
     }
-    rns::named_bar(1, kThreads);
+    rns::named_bar(1 + g, 128);
 
     for (int i = 0; i < kLweN; ++i) {
-      // Every gate of the block runs every step in lockstep (block-wide
-      // barriers keep all warps in the same code region).  A zero rotation
-      // (or an inactive slot) gives D = 0, whose digits are all zero, so the
-      // step adds exactly zero.
+      // A zero rotation (or an inactive slot) gives D = 0, whose digits are
+      // all zero, so the step adds exactly zero.
       const int rot = active ? __ldg(ab + i) : 0;
       uint32_t w[16];
       uint32_t X[2][2][8];  // [prime][output polynomial][position]
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
           v[0][n2] = rns::pretwist<0>(u + (rns::P<0>() - 512u), n2);
           v[1][n2] = rns::pretwist<1>(u + (rns::P<1>() - 512u), n2);
         }
-        rns::forward(v, Y, buf, t, 1, kThreads, tw_fwd);
+        rns::forward(v, Y, buf, t, 1 + g, 128, tw_fwd);
         wait_slot(smem_u32(full + slot), uint32_t(chunk / NSLOT) & 1u, abort, err);
         // X[o] += Y[0] * key(c=0, p, o) + Y[1] * key(c=1, p, o), per prime;
         // key words are (k mod p0, k mod p1) in Montgomery form.
@@ -309,18 +309,18 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
             X[1][o][d] = rns::fold<1, 4>(X[1][o][d]);
           }
         uint32_t v[2][16];
-        rns::inverse(X, v, buf, t, 1, kThreads, tw_inv);
+        rns::inverse(X, v, buf, t, 1 + g, 128, tw_inv);
         uint32_t *dst = acc + P * kRingN + n1;
 #pragma unroll
         for (int n2 = 0; n2 < 16; ++n2) dst[64 * n2] += rns::lift32(v[0][n2], v[1][n2]);
       }
-      rns::named_bar(1, kThreads);
+      rns::named_bar(1 + g, 128);
     }
     if (active) {
       uint32_t *out = acc_out + size_t(job) * 2 * kRingN;
       for (int j = t; j < 2 * kRingN; j += 128) out[j] = acc[j];
     }
-    rns::named_bar(1, kThreads);
+    rns::named_bar(1 + g, 128);
   }
 }
 

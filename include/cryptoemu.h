@@ -172,6 +172,15 @@ ce_status ce_negacyclic_mul_device(ce_ctx *ctx, const int16_t *d_d,
  * autotuned choice.  Applies to later calls. */
 ce_status ce_set_blind_rotate_config(ce_ctx *ctx, int gates_per_block,
                                      int blocks_per_sm);
+/* Engine of the fused sample extraction + key switching (§3: one key switch
+ * per gate): 0 = automatic (tensor cores for single-client launches of at
+ * least 32 outputs, CUDA cores otherwise), 1 = CUDA cores always, 2 = tensor
+ * cores for every single-client launch.  On the tensor cores the key switch
+ * is the exact product of a one-hot digit matrix and the key split into three
+ * 11-bit fp16 limbs (fp32 sums of at most 8192 terms below 2^11 are exact);
+ * both engines give bit-identical results.  CE_EINVAL for other values.
+ * Applies to later calls. */
+ce_status ce_set_keyswitch_config(ce_ctx *ctx, int engine);
 /* Waits for the context's stream and reports a device-side failure of the
  * asynchronous calls since the previous check (CE_ETIMEOUT when a bounded
  * device wait expired). */

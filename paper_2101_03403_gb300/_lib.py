@@ -66,6 +66,7 @@ def lib() -> ctypes.CDLL:
         "ce_mux_batch_device": (i32, [vp, i32, vp, vp, vp, vp, sz, vp]),
         "ce_negacyclic_mul_device": (i32, [vp, vp, vp, vp, sz, vp]),
         "ce_set_blind_rotate_config": (i32, [vp, i32, i32]),
+        "ce_set_keyswitch_config": (i32, [vp, i32]),
         "ce_last_launch_count": (i32, [vp]),
         "ce_synchronize": (i32, [vp]),
         "ce_profile_enable": (i32, [vp, i32]),
@@ -298,6 +299,11 @@ def ce_negacyclic_mul_device(ctx: Context, d_d, d_k, d_out, n: int, stream=None)
 def ce_set_blind_rotate_config(ctx: Context, gates_per_block: int, blocks_per_sm: int = 0):
     _check(lib().ce_set_blind_rotate_config(ctx.ptr, gates_per_block, blocks_per_sm),
            "ce_set_blind_rotate_config")
+
+
+def ce_set_keyswitch_config(ctx: Context, engine: int):
+    """0 automatic, 1 CUDA cores, 2 tensor cores (single-client launches)."""
+    _check(lib().ce_set_keyswitch_config(ctx.ptr, engine), "ce_set_keyswitch_config")
 
 
 def ce_last_launch_count(ctx: Context) -> int:

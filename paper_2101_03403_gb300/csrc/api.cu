@@ -170,15 +170,28 @@ ce_status run_path(ce_ctx *ctx, Client *cl, int mode, const uint8_t *ops, const 
   });
   if (e != cudaSuccess) return cuda_fail(e, "blind_rotate");
   ++launches;
-  int tile, jsplit;
-  ks_config(ctx, n, &tile, &jsplit);
-  if (jsplit > 1) {
-    e = cudaMemsetAsync(out, 0, n * kLweWords * sizeof(uint32_t), st);
-    if (e != cudaSuccess) return cuda_fail(e, "memset");
+  if (ks_use_tensor(ctx, n)) {
+    int n_tile, out_tiles, ksplit;
+    keyswitch_tc_shape(ctx->sms, int(n), &n_tile, &out_tiles, &ksplit);
+    if (ksplit > 1) {
+      e = cudaMemsetAsync(out, 0, n * kLweWords * sizeof(uint32_t), st);
+      if (e != cudaSuccess) return cuda_fail(e, "memset");
+    }
+    e = ce::timed(ctx, 2, st, [&] {
+      return launch_keyswitch_tc(ctx->acc, cl->ksk_planes, nullptr, out, int(n), mode != 0 ? 1 : 0,
+                                 n_tile, out_tiles, ksplit, ctx->err, st);
+    });
+  } else {
+    int tile, jsplit;
+    ks_config(ctx, n, &tile, &jsplit);
+    if (jsplit > 1) {
+      e = cudaMemsetAsync(out, 0, n * kLweWords * sizeof(uint32_t), st);
+      if (e != cudaSuccess) return cuda_fail(e, "memset");
+    }
+    e = ce::timed(ctx, 2, st, [&] {
+      return launch_extract_keyswitch(ctx->acc, cl->ksk, out, int(n), mode != 0, tile, jsplit, st);
+    });
   }
-  e = ce::timed(ctx, 2, st, [&] {
-    return launch_extract_keyswitch(ctx->acc, cl->ksk, out, int(n), mode != 0, tile, jsplit, st);
-  });
   if (e != cudaSuccess) return cuda_fail(e, "extract_keyswitch");
   ++launches;
   ctx->last_launches = launches;
@@ -243,6 +256,7 @@ extern "C" void ce_destroy(ce_ctx *ctx) {
   for (auto &c : ctx->clients) {
     cudaFree(c.bsk);
     cudaFree(c.ksk);
+    cudaFree(c.ksk_planes);
   }
   cudaFree(ctx->tw);
   cudaFree(ctx->err);
@@ -275,10 +289,12 @@ extern "C" ce_status ce_client_admit(ce_ctx *ctx, const void *cloud_key, size_t 
   uint32_t *coef = nullptr;
   cudaError_t e = cudaMalloc(&cl.bsk, kBskNttBytes);
   if (e == cudaSuccess) e = cudaMalloc(&cl.ksk, kKskDevBytes);
+  if (e == cudaSuccess) e = cudaMalloc(&cl.ksk_planes, kKsPlaneBytes);
   if (e == cudaSuccess) e = cudaMalloc(&coef, size_t(CE_BSK_WORDS) * 4);
   if (e != cudaSuccess) {
     cudaFree(cl.bsk);
     cudaFree(cl.ksk);
+    cudaFree(cl.ksk_planes);
     cudaFree(coef);
     return set_error(CE_ENOMEM, "ce_client_admit: device allocation failed");
   }
@@ -298,11 +314,13 @@ extern "C" ce_status ce_client_admit(ce_ctx *ctx, const void *cloud_key, size_t 
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(cl.ksk, kd.data(), kKskDevBytes, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = launch_bsk_to_transform(coef, cl.bsk, ctx->tw, st);
+  if (e == cudaSuccess) e = launch_ksk_to_planes(cl.ksk, cl.ksk_planes, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(coef);
   if (e != cudaSuccess) {
     cudaFree(cl.bsk);
     cudaFree(cl.ksk);
+    cudaFree(cl.ksk_planes);
     return cuda_fail(e, "ce_client_admit");
   }
   cl.live = true;
@@ -333,6 +351,7 @@ extern "C" ce_status ce_client_evict(ce_ctx *ctx, int client_id) {
   engine_drop_client(ctx->engine, client_id);
   cudaFree(cl->bsk);
   cudaFree(cl->ksk);
+  cudaFree(cl->ksk_planes);
   *cl = Client();
   ctx->used -= kClientBytes;
   return CE_OK;
@@ -422,6 +441,15 @@ extern "C" ce_status ce_set_blind_rotate_config(ce_ctx *ctx, int gates_per_block
   return CE_OK;
 }
 
+extern "C" ce_status ce_set_keyswitch_config(ce_ctx *ctx, int engine) {
+  if (!ctx) return set_error(CE_EINVAL, "ce_set_keyswitch_config: null context");
+  if (engine < 0 || engine > 2)
+    return set_error(CE_EINVAL, "key-switch engine must be 0 (auto), 1 (CUDA cores) or 2 "
+                                "(tensor cores)");
+  ctx->cfg_ks = engine;
+  return CE_OK;
+}
+
 extern "C" int ce_last_launch_count(ce_ctx *ctx) { return ctx ? ctx->last_launches : 0; }
 
 extern "C" ce_status ce_synchronize(ce_ctx *ctx) {
@@ -490,6 +518,13 @@ namespace ce {
 ce_status cuda_error(cudaError_t e, const char *where) { return cuda_fail(e, where); }
 ce_status ensure_job_scratch(ce_ctx *ctx, size_t jobs) { return ensure_jobs(ctx, jobs); }
 void br_shape(const ce_ctx *ctx, size_t jobs, int *G, int *blocks) { br_config(ctx, jobs, G, blocks); }
+// Tensor cores from 32 outputs (automatic): below that the CUDA-core kernel's
+// j-split keeps more SMs busy for the few outputs.
+bool ks_use_tensor(const ce_ctx *ctx, size_t n_out) {
+  if (ctx->cfg_ks == 1) return false;
+  if (ctx->cfg_ks == 2) return n_out > 0;
+  return n_out >= 32;
+}
 void ks_shape(const ce_ctx *ctx, size_t n_out, int *tile, int *jsplit) {
   ks_config(ctx, n_out, tile, jsplit);
 }

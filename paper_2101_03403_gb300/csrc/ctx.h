@@ -13,12 +13,16 @@ namespace ce {
 
 constexpr uint64_t kBskNttBytes = kBskNttWords * 8;
 constexpr uint64_t kKskDevBytes = kKskDevWords * 4;
-constexpr uint64_t kClientBytes = kBskNttBytes + kKskDevBytes;
+// fp16 limb planes of the key-switching key for the tensor-core key switch:
+// [4 word tiles][512 stages][3 limbs][128 words x 48] (keyswitch_tc.cu).
+constexpr uint64_t kKsPlaneBytes = uint64_t(4) * 512 * 3 * 128 * 48 * 2;
+constexpr uint64_t kClientBytes = kBskNttBytes + kKskDevBytes + kKsPlaneBytes;
 
 struct Client {
   bool live = false;
   uint64_t *bsk = nullptr;  // transform-domain bootstrapping key
   uint32_t *ksk = nullptr;  // [j][q][v-1][512]
+  uint16_t *ksk_planes = nullptr;  // fp16 limb planes for the tensor-core key switch
 };
 
 class Engine;  // netlist engine (engine.cu), created on first use
@@ -41,6 +45,7 @@ struct ce_ctx {
   uint32_t *io_a = nullptr, *io_b = nullptr, *io_out = nullptr;
   size_t io_cap = 0;
   int cfg_g = 0, cfg_bps = 0;
+  int cfg_ks = 0;  // key switch: 0 automatic, 1 CUDA cores, 2 tensor cores
   int last_launches = 0;
   // Optional per-kernel timing: event pairs recorded around each launch on
   // the launching stream, summed by ce_profile_read.
@@ -60,6 +65,8 @@ ce_status cuda_error(cudaError_t e, const char *where);
 ce_status ensure_job_scratch(ce_ctx *ctx, size_t jobs);
 cudaEvent_t take_event(ce_ctx *ctx);
 void br_shape(const ce_ctx *ctx, size_t jobs, int *G, int *blocks);
+// Whether a single-client key switch of n_out outputs runs on the tensor cores.
+bool ks_use_tensor(const ce_ctx *ctx, size_t n_out);
 void ks_shape(const ce_ctx *ctx, size_t n_out, int *tile, int *jsplit);
 void engine_destroy(Engine *e);
 void engine_drop_client(Engine *e, int client);

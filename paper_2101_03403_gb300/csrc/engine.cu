@@ -76,6 +76,7 @@ struct TickDesc {
   std::vector<const uint64_t *> grp_bsk;
   std::vector<const uint32_t *> tile_ksk;
   int G = 1, blocks = 1, tile = 1, jsplit = 1;
+  const uint16_t *ks_planes = nullptr;  // single-client tick on the tensor-core key switch
 };
 
 size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -106,6 +107,7 @@ struct Plan {
   struct Level {
     size_t jobs_off, outs_off, bsk_off, ksk_off;
     int n_jobs, n_outs, G, blocks, tile, jsplit;
+    const uint16_t *ks_planes;
   };
   std::vector<Level> levels;
   size_t map_off = 0;
@@ -304,6 +306,11 @@ class Engine {
       while ((t.outs.size() - out0) % t.tile) t.outs.push_back(GateOut{int32_t(job0), -1, kSlotSink, 0});
       for (size_t o = out0; o < t.outs.size(); o += t.tile) t.tile_ksk.push_back(cl.ksk);
     }
+    // one client: the key switch may run on the tensor cores with its planes
+    t.ks_planes = nullptr;
+    if (!order.empty() && order.front()->client == order.back()->client &&
+        ks_use_tensor(ctx, total_outs))
+      t.ks_planes = ctx->clients[order.front()->client].ksk_planes;
     // the padded batch may need more blocks than the unpadded estimate
     const size_t groups = t.jobs.size() / (t.G == 3 ? 1 : t.G);
     t.blocks = int(std::min<size_t>(groups, size_t(ctx->sms) * (t.G == 1 ? 2 : 1)));
@@ -354,7 +361,8 @@ class Engine {
   // switching into the arena.
   ce_status launch_level(const GateJob *jobs, int n_jobs, const GateOut *outs, int n_outs,
                          const uint64_t *const *grp_bsk, const uint32_t *const *tile_ksk, int G,
-                         int blocks, int tile, int jsplit, cudaStream_t st, int *launches) {
+                         int blocks, int tile, int jsplit, const uint16_t *ks_planes,
+                         cudaStream_t st, int *launches) {
     ce_status s = ensure_job_scratch(ctx, n_jobs);
     if (s != CE_OK) return s;
     cudaError_t e = timed(ctx, 0, st, [&] {
@@ -365,14 +373,26 @@ class Engine {
         return launch_blind_rotate(nullptr, ctx->abar, ctx->acc, n_jobs, ctx->tw, ctx->err, G,
                                    blocks, st, grp_bsk);
       });
-    if (e == cudaSuccess && jsplit > 1) e = launch_zero_slots(outs, arena, n_outs, st);
-    if (e == cudaSuccess)
-      e = timed(ctx, 2, st, [&] {
-        return launch_extract_keyswitch_ex(ctx->acc, nullptr, tile_ksk, outs, arena, n_outs, 2,
-                                           tile, jsplit, st);
-      });
+    int split = jsplit;
+    if (ks_planes) {
+      int n_tile, out_tiles;
+      keyswitch_tc_shape(ctx->sms, n_outs, &n_tile, &out_tiles, &split);
+      if (e == cudaSuccess && split > 1) e = launch_zero_slots(outs, arena, n_outs, st);
+      if (e == cudaSuccess)
+        e = timed(ctx, 2, st, [&] {
+          return launch_keyswitch_tc(ctx->acc, ks_planes, outs, arena, n_outs, 2, n_tile,
+                                     out_tiles, split, ctx->err, st);
+        });
+    } else {
+      if (e == cudaSuccess && jsplit > 1) e = launch_zero_slots(outs, arena, n_outs, st);
+      if (e == cudaSuccess)
+        e = timed(ctx, 2, st, [&] {
+          return launch_extract_keyswitch_ex(ctx->acc, nullptr, tile_ksk, outs, arena, n_outs, 2,
+                                             tile, jsplit, st);
+        });
+    }
     if (e != cudaSuccess) return cuda_error(e, "engine level launch");
-    *launches += 3 + (jsplit > 1 ? 1 : 0);
+    *launches += 3 + (split > 1 ? 1 : 0);
     return CE_OK;
   }
 
@@ -388,7 +408,7 @@ class Engine {
                      reinterpret_cast<const GateOut *>(dev + offs[1]), int(t.outs.size()),
                      reinterpret_cast<const uint64_t *const *>(dev + offs[2]),
                      reinterpret_cast<const uint32_t *const *>(dev + offs[3]), t.G, t.blocks,
-                     t.tile, t.jsplit, st, launches);
+                     t.tile, t.jsplit, t.ks_planes, st, launches);
     if (s != CE_OK) return s;
     for (Instance *in : act) ++in->level;
     return CE_OK;
@@ -473,6 +493,7 @@ class Engine {
       lv.blocks = t.blocks;
       lv.tile = t.tile;
       lv.jsplit = t.jsplit;
+      lv.ks_planes = t.ks_planes;
       p->max_jobs = std::max(p->max_jobs, t.jobs.size());
       lv.jobs_off = put(t.jobs.data(), t.jobs.size() * sizeof(GateJob));
       lv.outs_off = put(t.outs.data(), t.outs.size() * sizeof(GateOut));
@@ -520,7 +541,7 @@ class Engine {
                        reinterpret_cast<const GateOut *>(p.d_desc + lv.outs_off), lv.n_outs,
                        reinterpret_cast<const uint64_t *const *>(p.d_desc + lv.bsk_off),
                        reinterpret_cast<const uint32_t *const *>(p.d_desc + lv.ksk_off),
-                       lv.G, lv.blocks, lv.tile, lv.jsplit, st, launches);
+                       lv.G, lv.blocks, lv.tile, lv.jsplit, lv.ks_planes, st, launches);
       if (s != CE_OK) return s;
     }
     copy_out_kernel<<<unsigned(p.n * p.n_out), 128, 0, st>>>(

@@ -47,6 +47,18 @@ cudaError_t launch_bsk_to_transform(const uint32_t *bsk, uint64_t *out, const ui
 cudaError_t launch_negacyclic_mul(const int16_t *d, const uint32_t *k, uint32_t *out, int n,
                                   const uint4 *tw, cudaStream_t st);
 
+// Key switching on the tensor cores (keyswitch_tc.cu): the key-switching
+// key as three fp16 limb planes (admission), and the fused extraction + key
+// switch as a one-hot x key matrix product.  mode as for
+// launch_extract_keyswitch_ex (0 packed, 1 MUX pairs, 2 descriptors).  With
+// ksplit > 1 the outputs must be zero and are accumulated atomically.
+size_t keyswitch_tc_plane_bytes();
+cudaError_t launch_ksk_to_planes(const uint32_t *ksk, uint16_t *planes, cudaStream_t st);
+void keyswitch_tc_shape(int sms, int n_out, int *n_tile, int *out_tiles, int *ksplit);
+cudaError_t launch_keyswitch_tc(const uint32_t *acc, const uint16_t *planes, const GateOut *outs,
+                                uint32_t *out, int n_out, int mode, int n_tile, int out_tiles,
+                                int ksplit, int *err, cudaStream_t st);
+
 struct GatePathResources {
   const uint64_t *bsk;   // transform-domain bootstrapping key of the client
   const uint32_t *ksk;   // device key-switching key of the client

@@ -23,8 +23,9 @@
 // K, SBO = 768 B between 8-row groups):
 //   - the key limbs were rearranged at admission into that layout, one
 //     contiguous 36 KB block per (word tile, stage), fetched by one bulk copy;
-//   - the one-hot operand is written by the CTA's threads from the extracted
-//     coefficients (three 16-byte stores per output and j).
+//   - a pre-pass extracts and rounds the coefficients into [j][output]
+//     (coalesced); the one-hot operand is written by the CTA's threads from
+//     them (three 16-byte stores per output and j), one stage read ahead.
 // One thread issues the MMAs of a stage (3 K-steps x 3 limbs) and commits
 // them to the stage's release barrier; a ring of four stages overlaps the
 // copies, the one-hot construction and the MMAs.  Every wait is bounded
@@ -153,9 +154,10 @@ __device__ __forceinline__ OutJobs out_jobs(int mode, const GateOut *outs, int o
 // of 16, <= 160); stages_per_cta: stages of K in one CTA.  With a K split the
 // outputs were zeroed and partial sums are added atomically (exact mod 2^32).
 __global__ void __launch_bounds__(128, 1) keyswitch_tc_kernel(
-    const uint32_t *__restrict__ acc, const uint8_t *__restrict__ planes,
-    const GateOut *__restrict__ outs, uint32_t *__restrict__ out, int n_out, int mode, int n_tile,
-    int stages_per_cta, int *__restrict__ err) {
+    const uint32_t *__restrict__ acc, const uint16_t *__restrict__ hr, int ldh,
+    const uint8_t *__restrict__ planes, const GateOut *__restrict__ outs,
+    uint32_t *__restrict__ out, int n_out, int mode, int n_tile, int stages_per_cta,
+    int *__restrict__ err) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   uint8_t *smem = smem_raw;
   uint8_t *sa = smem;
@@ -201,25 +203,36 @@ __global__ void __launch_bounds__(128, 1) keyswitch_tc_kernel(
       issue_stage_copy(sa + size_t(s) * kTcABytes, smem_u32(full + s),
                        a_src + size_t(s) * kTcABytes);
 
+  // Rounded coefficients of this thread's items (item it: j' = it / n_tile,
+  // output o0 + it % n_tile), loaded one stage ahead; 0xFFFFFFFF marks a
+  // padding row (all-zero one-hot).
+  constexpr int kItems = (2 * kTcNMax + 127) / 128;
+  auto load_h = [&](int stage, uint32_t (&hv)[kItems]) {
+#pragma unroll
+    for (int u = 0; u < kItems; ++u) {
+      const int it = t + 128 * u;
+      hv[u] = 0xFFFFFFFFu;
+      if (it < 2 * n_tile && stage < n_stages) {
+        const int jj = it >= n_tile, ol = it - jj * n_tile, o = o0 + ol;
+        if (o < n_out) hv[u] = hr[size_t((s0 + stage) * kTcJPerStage + jj) * ldh + o];
+      }
+    }
+  };
+  uint32_t h_cur[kItems], h_next[kItems];
+  load_h(0, h_cur);
+
   for (int i = 0; i < n_stages; ++i) {
     const int slot = i % kTcSlots;
-    const int jbase = (s0 + i) * kTcJPerStage;
+    load_h(i + 1, h_next);
     // One-hot operand of this stage: rows = outputs of the tile, K = (j', d, q).
     uint8_t *b = sb + size_t(slot) * kTcBBytes;
-    for (int it = t; it < n_tile * kTcJPerStage; it += 128) {
-      const int ol = it >> 1, jj = it & 1, o = o0 + ol, j = jbase + jj;
-      uint32_t h = 0;  // rounded coefficient; a padding row stays all zero
-      const bool live = o < n_out;
-      if (live) {
-        const OutJobs jb = out_jobs(mode, outs, o);
-        const uint32_t *A = acc + size_t(jb.j1) * 2 * kRingN;
-        uint32_t a = (j == 0) ? A[0] : 0u - A[kRingN - j];
-        if (jb.j2 >= 0) {
-          const uint32_t *A2 = acc + size_t(jb.j2) * 2 * kRingN;
-          a += (j == 0) ? A2[0] : 0u - A2[kRingN - j];
-        }
-        h = (a + 0x8000u) >> 16;
-      }
+#pragma unroll
+    for (int u = 0; u < kItems; ++u) {
+      const int it = t + 128 * u;
+      if (it >= 2 * n_tile) break;
+      const int jj = it >= n_tile, ol = it - jj * n_tile;
+      const uint32_t h = h_cur[u];
+      const bool live = h != 0xFFFFFFFFu;
       uint8_t *row = b + (ol >> 3) * kTcSbo + (ol & 7) * 16 + jj * 3 * kTcLbo;
 #pragma unroll
       for (int d = 1; d <= 3; ++d) {
@@ -235,6 +248,8 @@ __global__ void __launch_bounds__(128, 1) keyswitch_tc_kernel(
         *reinterpret_cast<uint4 *>(row + (d - 1) * kTcLbo) = make_uint4(w[0], w[1], w[2], w[3]);
       }
     }
+#pragma unroll
+    for (int u = 0; u < kItems; ++u) h_cur[u] = h_next[u];
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (t == 0 && !*abort) {
@@ -346,6 +361,39 @@ __global__ void __launch_bounds__(128, 1) keyswitch_tc_kernel(
                  : "memory");
 }
 
+// Sample extraction + rounding, h[j][o] = round16(a'_j) of output o with
+// a'_0 = A_0, a'_j = -A_{N-j} (A = the output's accumulator, or the sum of
+// its two for a MUX), stored with outputs contiguous so that the key switch
+// reads a stage's coefficients coalesced.  Block (32 outputs, 32 j): reads
+// along j, writes along o through a shared-memory transpose.
+__global__ void __launch_bounds__(256) ks_round_kernel(const uint32_t *__restrict__ acc,
+                                                       const GateOut *__restrict__ outs, int mode,
+                                                       int n_out, uint16_t *__restrict__ hr,
+                                                       int ldh) {
+  __shared__ uint16_t tile[32][33];
+  const int o0 = blockIdx.x * 32, j0 = blockIdx.y * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {
+    const int o = o0 + r, j = j0 + tx;
+    uint16_t h = 0;
+    if (o < n_out) {
+      const OutJobs jb = out_jobs(mode, outs, o);
+      const uint32_t *A = acc + size_t(jb.j1) * 2 * kRingN;
+      uint32_t a = (j == 0) ? A[0] : 0u - A[kRingN - j];
+      if (jb.j2 >= 0) {
+        const uint32_t *A2 = acc + size_t(jb.j2) * 2 * kRingN;
+        a += (j == 0) ? A2[0] : 0u - A2[kRingN - j];
+      }
+      h = uint16_t((a + 0x8000u) >> 16);
+    }
+    tile[r][tx] = h;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int j = j0 + r, o = o0 + tx;
+    if (o < n_out) hr[size_t(j) * ldh + o] = tile[tx][r];
+  }
+}
+
 // Admission: the device key-switching key [j][q][d-1][512] (uint32) to the
 // three fp16 limb planes, tiled [word tile][stage][limb][core-matrix tile].
 // Block (word tile, stage); K within a stage is k = 24 j' + 8 (d - 1) + q,
@@ -398,17 +446,22 @@ void keyswitch_tc_shape(int sms, int n_out, int *n_tile, int *out_tiles, int *ks
 
 cudaError_t launch_keyswitch_tc(const uint32_t *acc, const uint16_t *planes, const GateOut *outs,
                                 uint32_t *out, int n_out, int mode, int n_tile, int out_tiles,
-                                int ksplit, int *err, cudaStream_t st) {
+                                int ksplit, uint16_t *h, int ldh, int *err, cudaStream_t st) {
   if (n_out <= 0) return cudaSuccess;
-  if (n_tile < 16 || n_tile > kTcNMax || n_tile % 16 || ksplit < 1 || kTcStages % ksplit)
+  if (n_tile < 16 || n_tile > kTcNMax || n_tile % 16 || ksplit < 1 || kTcStages % ksplit ||
+      ldh < n_out || size_t(out_tiles) * n_tile < size_t(n_out))
     return cudaErrorInvalidValue;
+  ks_round_kernel<<<dim3((n_out + 31) / 32, kRingN / 32), 256, 0, st>>>(acc, outs, mode, n_out, h,
+                                                                         ldh);
+  cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess) return le;
   cudaError_t e = cudaFuncSetAttribute(keyswitch_tc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(TcSmem::kTotal));
   if (e != cudaSuccess) return e;
   const dim3 grid(kTcWordTiles, out_tiles, ksplit);
   keyswitch_tc_kernel<<<grid, 128, TcSmem::kTotal, st>>>(
-      acc, reinterpret_cast<const uint8_t *>(planes), outs, out, n_out, mode, n_tile,
+      acc, h, ldh, reinterpret_cast<const uint8_t *>(planes), outs, out, n_out, mode, n_tile,
       kTcStages / ksplit, err);
   return cudaGetLastError();
 }

@@ -187,12 +187,14 @@ RNS_HD void bfly1(uint32_t &a, uint32_t &b) {
   b = fold<Q, 4>(d);
 }
 
-// Low 32 bits of the centred integer with residues r0 (mod p0) and r1
-// (mod p1), each given in [0, 4p).
+// Low 32 bits of the centred integer V (|V| < P/2) with residues r0 (mod p0)
+// and r1 (mod p1), each given in [0, 4p).  Garner's formula works on any
+// representatives: h = (r1 - r0) p0^-1 mod p1 (the offset 5 p1 > 4 p0 keeps
+// the difference positive, below 9 p1 < 2^32), S = r0 + h p0 = V (mod P) with
+// S in [0, P + 3 p0); V = S - P exactly when S > P/2 (for S >= P that is the
+// representative S - P in [0, 3 p0)).
 RNS_HD uint32_t lift32(uint32_t r0, uint32_t r1) {
-  r0 = fold<0, 1>(fold<0, 2>(r0));
-  r1 = fold<1, 1>(fold<1, 2>(r1));
-  uint32_t h = shoup<1>(r1 + 2 * P<1>() - r0, kCrt, kCrtP);
+  uint32_t h = shoup<1>(r1 + 5 * P<1>() - r0, kCrt, kCrtP);
   h = fold<1, 1>(h);
   const uint64_t s = r0 + uint64_t(h) * P<0>();
   return uint32_t(s) - (s > (kPP >> 1) ? uint32_t(kPP) : 0u);

@@ -181,6 +181,14 @@ ce_status ce_set_blind_rotate_config(ce_ctx *ctx, int gates_per_block,
  * both engines give bit-identical results.  CE_EINVAL for other values.
  * Applies to later calls. */
 ce_status ce_set_keyswitch_config(ce_ctx *ctx, int engine);
+/* Failure-detection self-test (the paper has no counterpart to this call):
+ * launches, on the context's stream, a kernel whose single thread waits on a
+ * shared-memory barrier that nothing completes, using the library's bounded
+ * device wait with limit_ns (1 us .. 2 s) instead of the kernels' 2 s.  The
+ * wait expires and raises the context's device error flag, so the next
+ * ce_synchronize returns CE_ETIMEOUT (and clears the flag); the context stays
+ * usable.  CE_EINVAL for a limit outside the range. */
+ce_status ce_selftest_device_wait(ce_ctx *ctx, uint64_t limit_ns);
 /* Waits for the context's stream and reports a device-side failure of the
  * asynchronous calls since the previous check (CE_ETIMEOUT when a bounded
  * device wait expired). */

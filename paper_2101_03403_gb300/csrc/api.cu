@@ -15,6 +15,7 @@ namespace ce {
 
 namespace {
 thread_local std::string g_last_error;
+constexpr uint64_t kMaxSelftestWaitNs = 2000000000ull;
 
 }  // namespace
 
@@ -465,6 +466,16 @@ extern "C" ce_status ce_synchronize(ce_ctx *ctx) {
   cudaError_t e = ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(e, "ce_synchronize");
   return check_device_error(ctx);
+}
+
+extern "C" ce_status ce_selftest_device_wait(ce_ctx *ctx, uint64_t limit_ns) {
+  if (!ctx) return set_error(CE_EINVAL, "ce_selftest_device_wait: null context");
+  if (limit_ns < 1000 || limit_ns > kMaxSelftestWaitNs)
+    return set_error(CE_EINVAL, "ce_selftest_device_wait: limit must lie in [1 us, 2 s]");
+  cudaSetDevice(ctx->device);
+  cudaError_t e = launch_wait_selftest(limit_ns, ctx->err, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ce_selftest_device_wait");
+  return CE_OK;
 }
 
 extern "C" ce_status ce_profile_enable(ce_ctx *ctx, int on) {

@@ -10,6 +10,7 @@
 
 #include <cstdint>
 
+#include "bounded_wait.cuh"
 #include "ce_internal.h"
 #include "launch.h"
 #include "rns_ntt.cuh"
@@ -109,41 +110,12 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ uint64_t global_timer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
-
-// Bounded wait for a slot's copy; on expiry the block records the error,
-// raises its abort flag and continues without waiting (results are then
-// invalid and the host reports CE_ETIMEOUT).
+// Bounded wait for a slot's copy (bounded_wait.cuh); on expiry the block
+// records the error, raises its abort flag and continues without waiting
+// (results are then invalid and the host reports CE_ETIMEOUT).
 __device__ __forceinline__ void wait_slot(uint32_t bar, uint32_t parity, volatile int *abort,
                                           int *err) {
-  if (mbar_try_wait(bar, parity)) return;
-  const uint64_t t0 = global_timer();
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort) return;
-    if (global_timer() - t0 > kWaitLimitNs) {
-      *abort = 1;
-      atomicExch(err, 1);
-      return;
-    }
-  }
+  (void)bounded_wait(bar, parity, abort, err);
 }
 
 __device__ __forceinline__ void issue_chunk(uint64_t *slot, uint32_t bar, const uint64_t *src) {
@@ -734,6 +706,25 @@ cudaError_t launch_bsk_to_transform(const uint32_t *bsk, uint64_t *out, const ui
                                     cudaStream_t st) {
   bsk_to_transform_kernel<<<kLweN * kGadgetL, 128, 0, st>>>(bsk, reinterpret_cast<uint2 *>(out),
                                                              tw);
+  return cudaGetLastError();
+}
+
+// Failure-detection self-test: one thread waits on an mbarrier whose phase
+// nothing completes (one expected arrival, none made), with the library's
+// bounded wait and a short limit; the wait expires and raises the error flag.
+__global__ void wait_selftest_kernel(uint64_t limit_ns, int *err) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
+    abort_flag = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) (void)bounded_wait(smem_addr(&bar), 0u, &abort_flag, err, limit_ns);
+}
+
+cudaError_t launch_wait_selftest(uint64_t limit_ns, int *err, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(limit_ns, err);
   return cudaGetLastError();
 }
 

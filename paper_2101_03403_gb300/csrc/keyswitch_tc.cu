@@ -34,6 +34,7 @@
 
 #include <cstdint>
 
+#include "bounded_wait.cuh"
 #include "ce_internal.h"
 #include "launch.h"
 
@@ -54,7 +55,6 @@ constexpr int kTcPlaneBytes = kTcM * kTcK * 2;        // 12,288
 constexpr int kTcABytes = 3 * kTcPlaneBytes;          // 36,864 per stage
 constexpr int kTcBBytes = kTcNMax * kTcK * 2;         // 15,360 per stage
 constexpr uint32_t kTcTmemCols = 512;
-constexpr uint64_t kTcWaitNs = 2000000000ull;
 
 static_assert(kTcWordTiles * kTcM == kKskRow, "word tiles cover a padded row");
 static_assert(3 * kTcNMax <= int(kTcTmemCols), "three accumulators fit in TMEM");
@@ -71,48 +71,13 @@ __host__ __device__ constexpr uint32_t cm_offset(int r, int k) {
   return uint32_t((r >> 3) * kTcSbo + (k >> 3) * kTcLbo + (r & 7) * 16 + (k & 7) * 2);
 }
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ uint64_t global_timer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait; false (with the error flag and abort raised) on expiry.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return smem_addr(p); }
+// Bounded waits of this kernel (bounded_wait.cuh).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort,
                                           int *err) {
-  if (mbar_try(bar, parity)) return true;
-  const uint64_t t0 = global_timer();
-  while (!mbar_try(bar, parity)) {
-    if (*abort) return false;
-    if (global_timer() - t0 > kTcWaitNs) {
-      *abort = 1;
-      atomicExch(err, 1);
-      return false;
-    }
-  }
-  return true;
+  return bounded_wait(bar, parity, abort, err);
 }
-
-// Wait used only after an abort, to let this CTA's own copies and MMAs
-// finish before its shared memory and TMEM are released (bounded as well).
-__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
-  const uint64_t t0 = global_timer();
-  while (!mbar_try(bar, parity))
-    if (global_timer() - t0 > kTcWaitNs) return;
-}
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) { drain_wait(bar, parity); }
 
 // Shared-memory matrix descriptor: start address, LBO, SBO (all >> 4),
 // descriptor version 1 at bit 46, no swizzle.

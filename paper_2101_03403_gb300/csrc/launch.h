@@ -60,6 +60,10 @@ cudaError_t launch_keyswitch_tc(const uint32_t *acc, const uint16_t *planes, con
                                 uint32_t *out, int n_out, int mode, int n_tile, int out_tiles,
                                 int ksplit, uint16_t *h, int ldh, int *err, cudaStream_t st);
 
+// Failure-detection self-test: a one-thread bounded wait on a barrier that
+// nothing completes, with the given limit (sets *err on expiry).
+cudaError_t launch_wait_selftest(uint64_t limit_ns, int *err, cudaStream_t st);
+
 struct GatePathResources {
   const uint64_t *bsk;   // transform-domain bootstrapping key of the client
   const uint32_t *ksk;   // device key-switching key of the client

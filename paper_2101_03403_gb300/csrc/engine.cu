@@ -917,6 +917,8 @@ static ce_status read_refs(ce_ctx *ctx, Engine *E, const SRef *refs_in, int coun
   std::lock_guard<std::recursive_mutex> lock(E->mu);
   SRef refs[kWidth];
   for (int j = 0; j < count; ++j) refs[j] = refs_in[j];
+  // Device-wide: the slots may have been written on a serving loop's stream.
+  cudaSetDevice(ctx->device);
   cudaError_t e = cudaDeviceSynchronize();
   for (int j = 0; j < count && e == cudaSuccess; ++j)
     e = cudaMemcpy(&out[j], E->arena + size_t(refs[j].slot) * kSlotWords, sizeof(ce_lwe),

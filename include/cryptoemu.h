@@ -117,12 +117,15 @@ const char *ce_last_error(void);
 
 /* Admit a client: copies its cloud key (CE_CLOUD_BYTES host bytes) to the
  * device and converts the bootstrapping key to the negacyclic-transform
- * domain used by the blind-rotation kernel (98,304 B per key bit).  Returns
- * CE_EADMIT when the client's device footprint would exceed the budget. */
+ * domain used by the blind-rotation kernel (98,304 B per key bit); the
+ * coefficient key stays resident too (for the tensor-core external product).
+ * Returns CE_EADMIT when the client's device footprint would exceed the
+ * budget. */
 ce_status ce_client_admit(ce_ctx *ctx, const void *cloud_key, size_t bytes,
                           int *client_id);
 ce_status ce_client_evict(ce_ctx *ctx, int client_id);
-/* Device bytes a client holds (keys + register file). */
+/* Device bytes a client holds at admission (keys + register file; the
+ * tensor-core external product adds its key form on first use). */
 uint64_t ce_client_footprint_bytes(void);
 
 /* ---------------------------------------------------------------- gates --- */
@@ -181,6 +184,20 @@ ce_status ce_set_blind_rotate_config(ce_ctx *ctx, int gates_per_block,
  * both engines give bit-identical results.  CE_EINVAL for other values.
  * Applies to later calls. */
 ce_status ce_set_keyswitch_config(ce_ctx *ctx, int engine);
+/* Form of the external products inside blind rotation (§3: the CMux steps
+ * of TFHE's bootstrapping): 0 = two-prime negacyclic transform on the CUDA
+ * cores (default); 1 = Toeplitz form on the tensor cores, where each CMux
+ * step of a batch is one [gates x 6144 digits] x [6144 x 2048] product with
+ * the key's negacyclic Toeplitz blocks, key words split into four balanced
+ * byte limbs and digits into two balanced 5-bit limbs (fp16 operands, fp32
+ * sums of 6144 products of at most 2^11: exact integers), recombined mod
+ * 2^32.  Both forms give bit-identical ciphertexts.  The tensor form applies
+ * to single-client launches (batches, and engine levels of one client); it
+ * builds the client's key as Hankel limb sequences (783,360,000 bytes,
+ * counted against the HBM budget: CE_EADMIT if over it) on the first call
+ * that uses it, so make that first call outside a stream capture.
+ * CE_EINVAL for other values.  Applies to later calls. */
+ce_status ce_set_external_product_form(ce_ctx *ctx, int form);
 /* Failure-detection self-test (the paper has no counterpart to this call):
  * launches, on the context's stream, a kernel whose single thread waits on a
  * shared-memory barrier that nothing completes, using the library's bounded

@@ -67,6 +67,7 @@ def lib() -> ctypes.CDLL:
         "ce_negacyclic_mul_device": (i32, [vp, vp, vp, vp, sz, vp]),
         "ce_set_blind_rotate_config": (i32, [vp, i32, i32]),
         "ce_set_keyswitch_config": (i32, [vp, i32]),
+        "ce_set_external_product_form": (i32, [vp, i32]),
         "ce_selftest_device_wait": (i32, [vp, ctypes.c_uint64]),
         "ce_last_launch_count": (i32, [vp]),
         "ce_synchronize": (i32, [vp]),
@@ -305,6 +306,11 @@ def ce_set_blind_rotate_config(ctx: Context, gates_per_block: int, blocks_per_sm
 def ce_set_keyswitch_config(ctx: Context, engine: int):
     """0 automatic, 1 CUDA cores, 2 tensor cores (single-client launches)."""
     _check(lib().ce_set_keyswitch_config(ctx.ptr, engine), "ce_set_keyswitch_config")
+
+
+def ce_set_external_product_form(ctx: Context, form: int):
+    """0 transform form (CUDA cores), 1 Toeplitz form (tensor cores)."""
+    _check(lib().ce_set_external_product_form(ctx.ptr, form), "ce_set_external_product_form")
 
 
 def ce_selftest_device_wait(ctx: Context, limit_ns: int):

@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcryptoemu.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["bootstrap_kernels.cu", "keyswitch_tc.cu", "api.cu", "noalloc.cu", "engine.cu", "serve.cu",
+SOURCES = ["bootstrap_kernels.cu", "keyswitch_tc.cu", "blind_rotate_tc.cu", "api.cu", "noalloc.cu", "engine.cu", "serve.cu",
            "host_keys.cpp", "netlist.cpp", "units_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")

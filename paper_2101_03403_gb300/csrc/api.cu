@@ -1,6 +1,7 @@
 // C ABI of the library: contexts, client admission, batched gates.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -62,8 +63,23 @@ ce_status cuda_fail(cudaError_t e, const char *where) {
 
 namespace {
 
+// Digit operand of the tensor-core external product, sized like the job
+// scratch once that form is selected.
+ce_status ensure_tt_digits(ce_ctx *ctx, size_t jobs) {
+  if (ctx->cfg_xp != 1 || (ctx->tt_digits && jobs <= ctx->tt_cap)) return CE_OK;
+  const size_t cap = std::max(jobs, ctx->job_cap);
+  cudaFree(ctx->tt_digits);
+  ctx->tt_digits = nullptr;
+  ctx->tt_cap = 0;
+  ++ctx->scratch_gen;
+  if (cudaMalloc(&ctx->tt_digits, blind_rotate_tc_digit_bytes(cap)) != cudaSuccess)
+    return set_error(CE_ENOMEM, "digit operand allocation failed");
+  ctx->tt_cap = cap;
+  return CE_OK;
+}
+
 ce_status ensure_jobs(ce_ctx *ctx, size_t jobs) {
-  if (jobs <= ctx->job_cap) return CE_OK;
+  if (jobs <= ctx->job_cap) return ensure_tt_digits(ctx, jobs);
   size_t cap = ctx->job_cap ? ctx->job_cap : 64;
   while (cap < jobs) cap *= 2;
   cudaFree(ctx->abar);  // synchronises with work still using the old scratch
@@ -81,7 +97,7 @@ ce_status ensure_jobs(ce_ctx *ctx, size_t jobs) {
   if (e == cudaSuccess) e = cudaMalloc(&ctx->ksh, size_t(kRingN) * ksh_ld(cap) * sizeof(uint16_t));
   if (e != cudaSuccess) return set_error(CE_ENOMEM, "scratch allocation failed");
   ctx->job_cap = cap;
-  return CE_OK;
+  return ensure_tt_digits(ctx, cap);
 }
 
 ce_status ensure_io(ce_ctx *ctx, size_t n) {
@@ -168,14 +184,25 @@ ce_status run_path(ce_ctx *ctx, Client *cl, int mode, const uint8_t *ops, const 
   });
   if (e != cudaSuccess) return cuda_fail(e, "lincomb_modswitch");
   ++launches;
-  int G, blocks;
-  br_config(ctx, jobs, &G, &blocks);
-  e = ce::timed(ctx, 1, st, [&] {
-    return launch_blind_rotate(cl->bsk, ctx->abar, ctx->acc, int(jobs), ctx->tw, ctx->err, G,
-                               blocks, st);
-  });
-  if (e != cudaSuccess) return cuda_fail(e, "blind_rotate");
-  ++launches;
+  if (ctx->cfg_xp == 1) {
+    s = ensure_hankel(ctx, cl);
+    if (s != CE_OK) return s;
+    const int ksplit = blind_rotate_tc_ksplit(ctx->sms, int(jobs));
+    e = ce::timed(ctx, 1, st, [&] {
+      return launch_blind_rotate_tc(cl->bsk_hankel, ctx->abar, ctx->acc, int(jobs),
+                                    ctx->tt_digits, ksplit, ctx->err, st, &launches);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "blind_rotate_tc");
+  } else {
+    int G, blocks;
+    br_config(ctx, jobs, &G, &blocks);
+    e = ce::timed(ctx, 1, st, [&] {
+      return launch_blind_rotate(cl->bsk, ctx->abar, ctx->acc, int(jobs), ctx->tw, ctx->err, G,
+                                 blocks, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(e, "blind_rotate");
+    ++launches;
+  }
   if (ks_use_tensor(ctx, n)) {
     int n_tile, out_tiles, ksplit;
     keyswitch_tc_shape(ctx->sms, int(n), &n_tile, &out_tiles, &ksplit);
@@ -265,8 +292,11 @@ extern "C" void ce_destroy(ce_ctx *ctx) {
     cudaFree(c.bsk);
     cudaFree(c.ksk);
     cudaFree(c.ksk_planes);
+    cudaFree(c.bsk_coef);
+    cudaFree(c.bsk_hankel);
   }
   cudaFree(ctx->tw);
+  cudaFree(ctx->tt_digits);
   cudaFree(ctx->ksh);
   cudaFree(ctx->err);
   cudaFree(ctx->abar);
@@ -325,13 +355,14 @@ extern "C" ce_status ce_client_admit(ce_ctx *ctx, const void *cloud_key, size_t 
   if (e == cudaSuccess) e = launch_bsk_to_transform(coef, cl.bsk, ctx->tw, st);
   if (e == cudaSuccess) e = launch_ksk_to_planes(cl.ksk, cl.ksk_planes, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(coef);
   if (e != cudaSuccess) {
     cudaFree(cl.bsk);
     cudaFree(cl.ksk);
     cudaFree(cl.ksk_planes);
+    cudaFree(coef);
     return cuda_fail(e, "ce_client_admit");
   }
+  cl.bsk_coef = coef;
   cl.live = true;
   int id = -1;
   for (size_t i = 0; i < ctx->clients.size(); ++i)
@@ -361,6 +392,11 @@ extern "C" ce_status ce_client_evict(ce_ctx *ctx, int client_id) {
   cudaFree(cl->bsk);
   cudaFree(cl->ksk);
   cudaFree(cl->ksk_planes);
+  cudaFree(cl->bsk_coef);
+  if (cl->bsk_hankel) {
+    cudaFree(cl->bsk_hankel);
+    ctx->used -= blind_rotate_tc_key_bytes();
+  }
   *cl = Client();
   ctx->used -= kClientBytes;
   return CE_OK;
@@ -459,6 +495,15 @@ extern "C" ce_status ce_set_keyswitch_config(ce_ctx *ctx, int engine) {
   return CE_OK;
 }
 
+extern "C" ce_status ce_set_external_product_form(ce_ctx *ctx, int form) {
+  if (!ctx) return set_error(CE_EINVAL, "ce_set_external_product_form: null context");
+  if (form < 0 || form > 1)
+    return set_error(CE_EINVAL, "external-product form must be 0 (transform, CUDA cores) or 1 "
+                                "(Toeplitz, tensor cores)");
+  ctx->cfg_xp = form;
+  return CE_OK;
+}
+
 extern "C" int ce_last_launch_count(ce_ctx *ctx) { return ctx ? ctx->last_launches : 0; }
 
 extern "C" ce_status ce_synchronize(ce_ctx *ctx) {
@@ -546,6 +591,25 @@ bool ks_use_tensor(const ce_ctx *ctx, size_t n_out) {
 }
 void ks_shape(const ce_ctx *ctx, size_t n_out, int *tile, int *jsplit) {
   ks_config(ctx, n_out, tile, jsplit);
+}
+ce_status ensure_hankel(ce_ctx *ctx, Client *cl) {
+  if (cl->bsk_hankel) return CE_OK;
+  const uint64_t bytes = blind_rotate_tc_key_bytes();
+  if (ctx->used + bytes > ctx->budget)
+    return set_error(CE_EADMIT, "tensor-core external product: key over the HBM budget");
+  if (cudaMalloc(&cl->bsk_hankel, bytes) != cudaSuccess) {
+    cl->bsk_hankel = nullptr;
+    return set_error(CE_ENOMEM, "tensor-core external product: key allocation failed");
+  }
+  cudaError_t e = launch_bsk_to_hankel(cl->bsk_coef, cl->bsk_hankel, ctx->stream);
+  if (e == cudaSuccess) e = ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaFree(cl->bsk_hankel);
+    cl->bsk_hankel = nullptr;
+    return cuda_error(e, "bsk_to_hankel");
+  }
+  ctx->used += bytes;
+  return CE_OK;
 }
 cudaEvent_t take_event(ce_ctx *ctx) {
   if (!ctx->ev_pool.empty()) {

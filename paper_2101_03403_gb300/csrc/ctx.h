@@ -16,13 +16,18 @@ constexpr uint64_t kKskDevBytes = kKskDevWords * 4;
 // fp16 limb planes of the key-switching key for the tensor-core key switch:
 // [4 word tiles][512 stages][3 limbs][128 words x 48] (keyswitch_tc.cu).
 constexpr uint64_t kKsPlaneBytes = uint64_t(4) * 512 * 3 * 128 * 48 * 2;
-constexpr uint64_t kClientBytes = kBskNttBytes + kKskDevBytes + kKsPlaneBytes;
+// Coefficient-domain bootstrapping key, kept for the tensor-core external
+// product, whose Hankel limb sequences are built from it on first use.
+constexpr uint64_t kBskCoefBytes = uint64_t(CE_BSK_WORDS) * 4;
+constexpr uint64_t kClientBytes = kBskNttBytes + kKskDevBytes + kKsPlaneBytes + kBskCoefBytes;
 
 struct Client {
   bool live = false;
   uint64_t *bsk = nullptr;  // transform-domain bootstrapping key
   uint32_t *ksk = nullptr;  // [j][q][v-1][512]
   uint16_t *ksk_planes = nullptr;  // fp16 limb planes for the tensor-core key switch
+  uint32_t *bsk_coef = nullptr;    // [i][r][o][N] coefficient key
+  uint16_t *bsk_hankel = nullptr;  // Hankel limb sequences (tensor-core external product)
 };
 
 class Engine;  // netlist engine (engine.cu), created on first use
@@ -47,6 +52,9 @@ struct ce_ctx {
   size_t io_cap = 0;
   int cfg_g = 0, cfg_bps = 0;
   int cfg_ks = 0;  // key switch: 0 automatic, 1 CUDA cores, 2 tensor cores
+  int cfg_xp = 0;  // external product: 0 transform (CUDA cores), 1 Toeplitz (tensor cores)
+  uint16_t *tt_digits = nullptr;  // digit operand of the tensor-core external product
+  size_t tt_cap = 0;              // jobs the digit operand holds
   int last_launches = 0;
   // Optional per-kernel timing: event pairs recorded around each launch on
   // the launching stream, summed by ce_profile_read.
@@ -71,6 +79,9 @@ inline int ksh_ld(size_t job_cap) { return int((job_cap + 16 + 7) / 8 * 8); }
 // Whether a single-client key switch of n_out outputs runs on the tensor cores.
 bool ks_use_tensor(const ce_ctx *ctx, size_t n_out);
 void ks_shape(const ce_ctx *ctx, size_t n_out, int *tile, int *jsplit);
+// Builds the client's Hankel limb sequences if missing (counted against the
+// context's HBM budget).
+ce_status ensure_hankel(ce_ctx *ctx, Client *cl);
 void engine_destroy(Engine *e);
 void engine_drop_client(Engine *e, int client);
 // Records an event pair around `launch` when profiling is on (kind 0, 1, 2).

@@ -77,6 +77,7 @@ struct TickDesc {
   std::vector<const uint32_t *> tile_ksk;
   int G = 1, blocks = 1, tile = 1, jsplit = 1;
   const uint16_t *ks_planes = nullptr;  // single-client tick on the tensor-core key switch
+  const uint16_t *br_hankel = nullptr;  // single-client tick on the tensor-core external product
 };
 
 size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -97,7 +98,7 @@ struct RegFile {
 };
 
 struct Plan {
-  int unit = 0, cond = 0, client = 0;
+  int unit = 0, cond = 0, client = 0, xp = 0;
   size_t n = 0;
   const uint32_t *d_in = nullptr;
   uint32_t *d_out = nullptr;
@@ -108,6 +109,7 @@ struct Plan {
     size_t jobs_off, outs_off, bsk_off, ksk_off;
     int n_jobs, n_outs, G, blocks, tile, jsplit;
     const uint16_t *ks_planes;
+    const uint16_t *br_hankel;
   };
   std::vector<Level> levels;
   size_t map_off = 0;
@@ -306,11 +308,19 @@ class Engine {
       while ((t.outs.size() - out0) % t.tile) t.outs.push_back(GateOut{int32_t(job0), -1, kSlotSink, 0});
       for (size_t o = out0; o < t.outs.size(); o += t.tile) t.tile_ksk.push_back(cl.ksk);
     }
-    // one client: the key switch may run on the tensor cores with its planes
+    // one client: the key switch may run on the tensor cores with its planes,
+    // and the external products too (Toeplitz form) when selected
     t.ks_planes = nullptr;
-    if (!order.empty() && order.front()->client == order.back()->client &&
-        ks_use_tensor(ctx, total_outs))
+    t.br_hankel = nullptr;
+    const bool one_client = !order.empty() && order.front()->client == order.back()->client;
+    if (one_client && ks_use_tensor(ctx, total_outs))
       t.ks_planes = ctx->clients[order.front()->client].ksk_planes;
+    if (one_client && ctx->cfg_xp == 1) {
+      Client &cl = ctx->clients[order.front()->client];
+      ce_status hs = ensure_hankel(ctx, &cl);
+      if (hs != CE_OK) return hs;
+      t.br_hankel = cl.bsk_hankel;
+    }
     // the padded batch may need more blocks than the unpadded estimate
     const size_t groups = t.jobs.size() / (t.G == 3 ? 1 : t.G);
     t.blocks = int(std::min<size_t>(groups, size_t(ctx->sms) * (t.G == 1 ? 2 : 1)));
@@ -362,17 +372,26 @@ class Engine {
   ce_status launch_level(const GateJob *jobs, int n_jobs, const GateOut *outs, int n_outs,
                          const uint64_t *const *grp_bsk, const uint32_t *const *tile_ksk, int G,
                          int blocks, int tile, int jsplit, const uint16_t *ks_planes,
-                         cudaStream_t st, int *launches) {
+                         const uint16_t *br_hankel, cudaStream_t st, int *launches) {
     ce_status s = ensure_job_scratch(ctx, n_jobs);
     if (s != CE_OK) return s;
     cudaError_t e = timed(ctx, 0, st, [&] {
       return launch_lincomb_gather(jobs, arena, ctx->abar, n_jobs, ctx->err, st);
     });
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && br_hankel) {
+      const int ksplit = blind_rotate_tc_ksplit(ctx->sms, n_jobs);
+      int tc_launches = 0;
+      e = timed(ctx, 1, st, [&] {
+        return launch_blind_rotate_tc(br_hankel, ctx->abar, ctx->acc, n_jobs, ctx->tt_digits,
+                                      ksplit, ctx->err, st, &tc_launches);
+      });
+      *launches += tc_launches - 1;  // one blind-rotation launch is counted below
+    } else if (e == cudaSuccess) {
       e = timed(ctx, 1, st, [&] {
         return launch_blind_rotate(nullptr, ctx->abar, ctx->acc, n_jobs, ctx->tw, ctx->err, G,
                                    blocks, st, grp_bsk);
       });
+    }
     int split = jsplit;
     if (ks_planes) {
       int n_tile, out_tiles;
@@ -410,7 +429,7 @@ class Engine {
                      reinterpret_cast<const GateOut *>(dev + offs[1]), int(t.outs.size()),
                      reinterpret_cast<const uint64_t *const *>(dev + offs[2]),
                      reinterpret_cast<const uint32_t *const *>(dev + offs[3]), t.G, t.blocks,
-                     t.tile, t.jsplit, t.ks_planes, st, launches);
+                     t.tile, t.jsplit, t.ks_planes, t.br_hankel, st, launches);
     if (s != CE_OK) return s;
     for (Instance *in : act) ++in->level;
     return CE_OK;
@@ -433,7 +452,7 @@ class Engine {
                       uint32_t *d_out, Plan **out) {
     for (auto &p : plans)
       if (p->unit == unit && p->cond == cond && p->client == client && p->n == n &&
-          p->d_in == d_in && p->d_out == d_out) {
+          p->d_in == d_in && p->d_out == d_out && p->xp == ctx->cfg_xp) {
         p->last_use = ++use_clock;
         *out = p.get();
         return CE_OK;
@@ -451,6 +470,7 @@ class Engine {
     p->unit = unit;
     p->cond = cond;
     p->client = client;
+    p->xp = ctx->cfg_xp;
     p->n = n;
     p->d_in = d_in;
     p->d_out = d_out;
@@ -496,6 +516,7 @@ class Engine {
       lv.tile = t.tile;
       lv.jsplit = t.jsplit;
       lv.ks_planes = t.ks_planes;
+      lv.br_hankel = t.br_hankel;
       p->max_jobs = std::max(p->max_jobs, t.jobs.size());
       lv.jobs_off = put(t.jobs.data(), t.jobs.size() * sizeof(GateJob));
       lv.outs_off = put(t.outs.data(), t.outs.size() * sizeof(GateOut));
@@ -543,7 +564,8 @@ class Engine {
                        reinterpret_cast<const GateOut *>(p.d_desc + lv.outs_off), lv.n_outs,
                        reinterpret_cast<const uint64_t *const *>(p.d_desc + lv.bsk_off),
                        reinterpret_cast<const uint32_t *const *>(p.d_desc + lv.ksk_off),
-                       lv.G, lv.blocks, lv.tile, lv.jsplit, lv.ks_planes, st, launches);
+                       lv.G, lv.blocks, lv.tile, lv.jsplit, lv.ks_planes, lv.br_hankel, st,
+                       launches);
       if (s != CE_OK) return s;
     }
     copy_out_kernel<<<unsigned(p.n * p.n_out), 128, 0, st>>>(

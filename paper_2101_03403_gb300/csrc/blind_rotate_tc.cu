@@ -31,6 +31,7 @@
 // each followed by an epilogue that recombines the limbs and adds into ACC.
 // Every wait is bounded (2 s on %globaltimer, then an error flag and an
 // orderly exit).
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -74,15 +75,8 @@ struct TtSmem {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return smem_addr(p); }
 
-// fp16 bit pattern of an integer with |x| < 2048 (exact).
-__host__ __device__ __forceinline__ uint16_t fp16_of_int(int x) {
-  if (x == 0) return 0;
-  const uint32_t s = x < 0 ? 0x8000u : 0u;
-  const uint32_t m = uint32_t(x < 0 ? -x : x);
-  int e = 0;
-  while ((m >> (e + 1)) != 0) ++e;
-  return uint16_t(s | uint32_t((15 + e) << 10) | ((m << (10 - e)) & 0x3FFu));
-}
+// fp16 bit pattern of an integer with |x| <= 2048 (the conversion is exact).
+__device__ __forceinline__ uint16_t fp16_of_int(int x) { return __half_as_ushort(__int2half_rn(x)); }
 
 // Balanced limb a of x (x = sum_a 2^(8a) limb_a mod 2^32, limb in [-128, 127]).
 __device__ __forceinline__ void byte_limbs(uint32_t x, int (&l)[kTtLimbs]) {

@@ -60,6 +60,12 @@ OPS_PER_GATE = 500 * (7 * BFLY_PER_CMUX + 2.5 * MAC_PER_CMUX)   # 317,440,000
 PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12                          # 40.27
 KERNEL_SOURCES = ["bootstrap_kernels.cu", "rns_ntt.cuh", "rns_arith.h"]
 N_PAIRS = 256
+# External-product forms compared on one gate batch (19 tiles of 128 gates:
+# two full waves of the tensor-core kernel's 16 x 19 CTAs on 152 SMs).
+XP_GATES = 2432
+# Tensor (Toeplitz) form: per CMux step and gate, eight limb products of the
+# [2048 x 6144] key block with the 6144 digits, 2 flops per multiply-add.
+XP_FLOPS_PER_GATE = 500 * 2 * 2048 * 6144 * 8                  # 1.0066e11
 
 
 def parse():
@@ -353,6 +359,9 @@ def run_ours(args, rank: int, world: int, local: int):
         assert decrypt_word(ce, sk, mo[i]) == (int(ma[i]) * int(mb[i])) & 0xFFFF, "wrong product"
     mul_boots = mul_n * ce.ce_unit_info("MUL")["n_bootstraps"]
 
+    forms = external_product_forms(ce, ctx, cid, stream, dev, rng, d_min, d_mout, mul_n) \
+        if rank == 0 else None
+
     br_ms, br_launches = prof["blind_rotate"]
     achieved = boots * args.steps * OPS_PER_GATE / (br_ms / 1e3) / 1e12
     roof = {"kernel": "blind_rotate", "bound": "alu", "achieved": achieved,
@@ -396,9 +405,89 @@ def run_ours(args, rank: int, world: int, local: int):
                         "h2d_bytes_per_step": int(host_in.nbytes),
                         "d2h_bytes_per_step": int(n * 16 * 501 * 4)},
                 "gpu_launches": launches, "roofline": roof, "clocks": clk.summary(),
-                "cpu_baseline": cpu}
+                "cpu_baseline": cpu, "external_product_forms": forms}
         print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def external_product_forms(ce, ctx, cid, stream, dev, rng, d_min, d_mout, mul_n):
+    """The blind rotation's external products in both forms on one batch of
+    XP_GATES seeded gates and on the MUL-64 unit: the two-prime transform on
+    the CUDA cores (default) and the Toeplitz contraction on the tensor cores.
+    Outputs must be identical; each form's dominant kernel is set against its
+    roofline (integer issue rate; measured tensor rate, fp16 = bf16 rate)."""
+    import torch
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        peaks = json.load(f)
+    n = XP_GATES
+
+    def dev_ct(shape):
+        x = rng.integers(0, 1 << 32, shape + (501,), dtype=np.uint64).astype(np.uint32)
+        return torch.from_numpy(x.view(np.int32)).to(dev)
+
+    a, b = dev_ct((n,)), dev_ct((n,))
+    ops = torch.from_numpy(rng.integers(0, 10, n).astype(np.uint8)).to(dev)
+    outs, res = {}, {}
+
+    def ev_ms(fn, reps):
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        return ts
+
+    for form, name in ((0, "transform_cuda_cores"), (1, "toeplitz_tensor_cores")):
+        ce.ce_set_external_product_form(ctx, form)
+        o = torch.empty((n, 501), dtype=torch.int32, device=dev)
+
+        def batch():
+            ce.ce_gates_batch_device(ctx, cid, ops, a, b, o, n, stream)
+
+        batch()                                   # the tensor form builds its key here
+        ce.ce_synchronize(ctx)
+        batch_ms = statistics.median(ev_ms(batch, 3))
+        ce.ce_profile_enable(ctx, True)
+        batch()
+        ce.ce_synchronize(ctx)
+        prof = ce.ce_profile_read(ctx)
+        ce.ce_profile_enable(ctx, False)
+        outs[form] = o.cpu()
+
+        def mul():
+            ce.ce_unit_eval_device(ctx, cid, "MUL", d_min, d_mout, mul_n, 0, stream)
+
+        mul()
+        torch.cuda.synchronize(dev)
+        mul_ms = statistics.median(ev_ms(mul, 2))
+        entry = {"gates_per_s": n / (batch_ms / 1e3), "batch_ms": batch_ms,
+                 "mul16_batch64_ms": mul_ms}
+        if form == 0:
+            ms = prof["blind_rotate"][0]
+            ach = n * OPS_PER_GATE / (ms / 1e3) / 1e12
+            entry["roofline"] = {"kernel": "blind_rotate", "bound": "alu", "achieved": ach,
+                                 "peak": PEAK_TOPS, "unit": "Tops/s (int32)",
+                                 "frac": ach / PEAK_TOPS}
+        else:
+            ms, cnt = prof["external_product_mma"]
+            ach = n * XP_FLOPS_PER_GATE / (ms / 1e3) / 1e12
+            peak = peaks["bf16_tflops_sustained"]
+            entry["roofline"] = {"kernel": "tt_mma", "bound": "tensor", "achieved": ach,
+                                 "peak": peak, "unit": "TFLOP/s (fp16)", "frac": ach / peak,
+                                 "frac_of_burst_peak": ach / peaks["bf16_tflops"],
+                                 "peak_note": "measured bf16 GEMM (sustained; fp16 runs at the "
+                                              "bf16 rate)",
+                                 "launches": cnt, "kernel_ms": ms,
+                                 "blind_rotate_ms": prof["blind_rotate"][0]}
+        res[name] = entry
+    ce.ce_set_external_product_form(ctx, 0)
+    assert torch.equal(outs[0], outs[1]), "external-product forms disagree"
+    res["identical_outputs"] = True
+    res["gates"] = n
+    return res
 
 
 def main():

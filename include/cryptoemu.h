@@ -349,8 +349,9 @@ ce_status ce_gates_batch_device_noalloc(ce_ctx *ctx, int client, const uint8_t *
  * the gate path is bracketed by CUDA events on its own stream.
  * ce_profile_read waits for them and returns, per kernel kind (0 = linear
  * combination + modulus switch, 1 = blind rotation, 2 = extraction + key
- * switching), the summed milliseconds and the launch count since the last
- * read. */
+ * switching, 3 = the MMA launches inside a tensor-core blind rotation, also
+ * counted in kind 1), the summed milliseconds and the launch count since the
+ * last read. */
 ce_status ce_profile_enable(ce_ctx *ctx, int on);
 ce_status ce_profile_read(ce_ctx *ctx, double *ms, int *launches, int kinds);
 

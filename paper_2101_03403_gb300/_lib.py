@@ -327,7 +327,7 @@ def ce_synchronize(ctx: Context):
     _check(lib().ce_synchronize(ctx.ptr), "ce_synchronize")
 
 
-KERNEL_KINDS = ["lincomb_modswitch", "blind_rotate", "extract_keyswitch"]
+KERNEL_KINDS = ["lincomb_modswitch", "blind_rotate", "extract_keyswitch", "external_product_mma"]
 
 
 def ce_profile_enable(ctx: Context, on: bool = True):

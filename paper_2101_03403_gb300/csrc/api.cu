@@ -190,8 +190,10 @@ ce_status run_path(ce_ctx *ctx, Client *cl, int mode, const uint8_t *ops, const 
     const int ksplit = blind_rotate_tc_ksplit(ctx->sms, int(jobs));
     e = ce::timed(ctx, 1, st, [&] {
       return launch_blind_rotate_tc(cl->bsk_hankel, ctx->abar, ctx->acc, int(jobs),
-                                    ctx->tt_digits, ksplit, ctx->err, st, &launches);
+                                    ctx->tt_digits, ksplit, ctx->err, st, &launches,
+                                    mma_events(ctx));
     });
+    keep_mma_events(ctx);
     if (e != cudaSuccess) return cuda_fail(e, "blind_rotate_tc");
   } else {
     int G, blocks;
@@ -610,6 +612,17 @@ ce_status ensure_hankel(ce_ctx *ctx, Client *cl) {
   }
   ctx->used += bytes;
   return CE_OK;
+}
+cudaEvent_t *mma_events(ce_ctx *ctx) {
+  if (!ctx->profile) return nullptr;
+  ctx->mma_ev.resize(2 * kLweN);
+  for (auto &e : ctx->mma_ev) e = take_event(ctx);
+  return ctx->mma_ev.data();
+}
+void keep_mma_events(ce_ctx *ctx) {
+  for (size_t i = 0; i + 1 < ctx->mma_ev.size(); i += 2)
+    ctx->timed.push_back({3, ctx->mma_ev[i], ctx->mma_ev[i + 1]});
+  ctx->mma_ev.clear();
 }
 cudaEvent_t take_event(ce_ctx *ctx) {
   if (!ctx->ev_pool.empty()) {

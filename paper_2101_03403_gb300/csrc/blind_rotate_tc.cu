@@ -434,17 +434,29 @@ cudaError_t launch_bsk_to_hankel(const uint32_t *bsk, uint16_t *hankel, cudaStre
   return cudaGetLastError();
 }
 
+// K split of a launch: the split k (a divisor of the 96 chunks) with the
+// least modelled time, waves(k) x (1/k + 0.12 [k > 1]) in units of one
+// CTA's full-K work: waves(k) = ceil(16 tiles k / sms), and 0.12 is the
+// measured extra cost of a CTA whose partial sums go through atomics.
 int blind_rotate_tc_ksplit(int sms, int n_jobs) {
   const int tiles = (n_jobs + kTtM - 1) / kTtM;
-  const int options[] = {8, 6, 4, 3, 2};
-  for (int k : options)
-    if (kTtCoefTiles * tiles * k <= sms) return k;
-  return 1;
+  const int options[] = {1, 2, 3, 4, 6, 8};
+  int best = 1;
+  double best_cost = 1e30;
+  for (int k : options) {
+    const int waves = (kTtCoefTiles * tiles * k + sms - 1) / sms;
+    const double cost = waves * (1.0 / k + (k > 1 ? 0.12 : 0.0));
+    if (cost < best_cost) {
+      best = k;
+      best_cost = cost;
+    }
+  }
+  return best;
 }
 
 cudaError_t launch_blind_rotate_tc(const uint16_t *hankel, const uint16_t *abar, uint32_t *acc,
                                    int n_jobs, uint16_t *digits, int ksplit, int *err,
-                                   cudaStream_t st, int *launches) {
+                                   cudaStream_t st, int *launches, cudaEvent_t *mma_ev) {
   if (n_jobs <= 0) return cudaSuccess;
   if (ksplit < 1 || kTtChunks % ksplit) return cudaErrorInvalidValue;
   const int n_tiles = (n_jobs + kTtM - 1) / kTtM;
@@ -463,9 +475,11 @@ cudaError_t launch_blind_rotate_tc(const uint16_t *hankel, const uint16_t *abar,
   for (int i = 0; i < kLweN; ++i) {
     tt_digits_kernel<<<n_tiles * (kTtM / 8), 256, dig_smem, st>>>(acc, abar, i, n_jobs, n_tiles,
                                                                   digits);
+    if (mma_ev) cudaEventRecord(mma_ev[2 * i], st);
     tt_mma_kernel<<<mma_grid, 192, TtSmem::kTotal, st>>>(digits, hankel + size_t(i) * step_words,
                                                          acc, n_jobs, n_tiles,
                                                          kTtChunks / ksplit, err);
+    if (mma_ev) cudaEventRecord(mma_ev[2 * i + 1], st);
   }
   e = cudaGetLastError();
   if (launches) *launches += 1 + 2 * kLweN;

@@ -62,6 +62,7 @@ struct ce_ctx {
   std::vector<cudaEvent_t> ev_pool;
   struct Timed { int kind; cudaEvent_t a, b; };
   std::vector<Timed> timed;
+  std::vector<cudaEvent_t> mma_ev;  // pending events of kind 3
   ce::Engine *engine = nullptr;
   // Autotuned blind-rotation shape: gates per block for measured job counts.
   std::vector<int> tune_jobs, tune_g;
@@ -85,6 +86,10 @@ ce_status ensure_hankel(ce_ctx *ctx, Client *cl);
 void engine_destroy(Engine *e);
 void engine_drop_client(Engine *e, int client);
 // Records an event pair around `launch` when profiling is on (kind 0, 1, 2).
+// Event pairs for the MMA launches of a tensor-core blind rotation (kind 3)
+// while profiling is on, else nullptr; keep_mma_events files them.
+cudaEvent_t *mma_events(ce_ctx *ctx);
+void keep_mma_events(ce_ctx *ctx);
 template <class F>
 cudaError_t timed(ce_ctx *ctx, int kind, cudaStream_t st, F launch) {
   if (!ctx->profile) return launch();

@@ -383,8 +383,9 @@ class Engine {
       int tc_launches = 0;
       e = timed(ctx, 1, st, [&] {
         return launch_blind_rotate_tc(br_hankel, ctx->abar, ctx->acc, n_jobs, ctx->tt_digits,
-                                      ksplit, ctx->err, st, &tc_launches);
+                                      ksplit, ctx->err, st, &tc_launches, mma_events(ctx));
       });
+      keep_mma_events(ctx);
       *launches += tc_launches - 1;  // one blind-rotation launch is counted below
     } else if (e == cudaSuccess) {
       e = timed(ctx, 1, st, [&] {

@@ -64,14 +64,16 @@ cudaError_t launch_keyswitch_tc(const uint32_t *acc, const uint16_t *planes, con
 // (blind_rotate_tc.cu).  hankel: the client's key as Hankel limb sequences
 // (blind_rotate_tc_key_bytes, built by launch_bsk_to_hankel from the
 // coefficient key); digits: scratch of blind_rotate_tc_digit_bytes(n_jobs).
-// Launches 1 + 2 n kernels; ACC layout as launch_blind_rotate.
+// Launches 1 + 2 n kernels; ACC layout as launch_blind_rotate.  mma_ev
+// (optional, 2 n events): recorded before and after each step's MMA launch.
 size_t blind_rotate_tc_key_bytes();
 size_t blind_rotate_tc_digit_bytes(size_t n_jobs);
 cudaError_t launch_bsk_to_hankel(const uint32_t *bsk, uint16_t *hankel, cudaStream_t st);
 int blind_rotate_tc_ksplit(int sms, int n_jobs);
 cudaError_t launch_blind_rotate_tc(const uint16_t *hankel, const uint16_t *abar, uint32_t *acc,
                                    int n_jobs, uint16_t *digits, int ksplit, int *err,
-                                   cudaStream_t st, int *launches);
+                                   cudaStream_t st, int *launches,
+                                   cudaEvent_t *mma_ev = nullptr);
 
 // Failure-detection self-test: a one-thread bounded wait on a barrier that
 // nothing completes, with the given limit (sets *err on expiry).

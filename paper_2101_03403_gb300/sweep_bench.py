@@ -1,6 +1,7 @@
 """Latency and throughput sweeps on one GPU (one JSON line):
 
   python -m paper_2101_03403_gb300.sweep_bench [--programs 32] [--reps 5]
+  python -m paper_2101_03403_gb300.sweep_bench --xp-gates 2432
 
 * gate batches: bootstrapped gates/s and batch latency for batch sizes from
   one gate to 9728 (autotuned launch shape per size);
@@ -9,6 +10,11 @@
 * register programs: 32 encrypted programs (one per client, lengths uniform
   in [8, 64], ADD/SUB/AND/ORR/LSL/LSL_IMM/CMP/CSEL/MOV/MOV_IMM) advancing
   together through ce_exec_multi, and the longest one alone.
+
+With --xp-gates N: one batch of N gates with the blind rotation's external
+products on the tensor cores (Toeplitz form), after one warm-up batch that
+also builds the key form; nothing else runs, so a profiler skips the
+admission (2 launches) and the warm-up batch (1005 launches for N >= 32).
 
 Inputs are seeded uniform 501-word ciphertexts (the bootstrapping path is a
 fixed function of any input, so timing does not need valid encryptions);
@@ -32,11 +38,46 @@ def pct(xs, q):
     return float(np.percentile(np.asarray(xs), q))
 
 
+def tensor_form_batch(n):
+    import torch
+
+    import paper_2101_03403_gb300 as ce
+    rng = np.random.default_rng(SEED)
+    sk = ce.ce_secret_keygen(SEED)
+    ctx = ce.ce_create(0)
+    cid = ce.ce_client_admit(ctx, ce.ce_cloud_keygen(sk, SEED))
+    st = torch.cuda.current_stream()
+
+    def ct():
+        x = rng.integers(0, 2 ** 32, (n, 501), dtype=np.uint64).astype(np.uint32)
+        return torch.from_numpy(x.view(np.int32)).cuda()
+
+    a, b = ct(), ct()
+    ops = torch.from_numpy(rng.integers(0, 10, n).astype(np.uint8)).cuda()
+    o = torch.empty((n, 501), dtype=torch.int32, device="cuda")
+    ce.ce_set_external_product_form(ctx, 1)
+    ms = []
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        ce.ce_gates_batch_device(ctx, cid, ops, a, b, o, n, st)
+        e1.record(st)
+        ce.ce_synchronize(ctx)
+        ms.append(e0.elapsed_time(e1))
+    print(json.dumps({"form": "toeplitz_tensor_cores", "gates": n, "warmup_ms": ms[0],
+                      "batch_ms": ms[1], "gates_per_s": n / ms[1] * 1e3,
+                      "launches": ce.ce_last_launch_count(ctx)}), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--programs", type=int, default=32)
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--xp-gates", type=int, default=0)
     args = ap.parse_args()
+    if args.xp_gates:
+        return tensor_form_batch(args.xp_gates)
     import torch
 
     import paper_2101_03403_gb300 as ce

@@ -7,9 +7,10 @@ key's negacyclic Toeplitz blocks, key words in four balanced byte limbs and
 digits in two balanced 5-bit limbs (fp16 operands, exact fp32 sums).
 Ciphertexts must equal the oracle word for word (all of them for small
 batches, sampled ones for large), and the transform form on every output:
-across gate tiles of 128 with ragged tails, each K split the launcher picks
-(8, 4, 3, 1 for 1, 2, 3 and 10+ tiles), zero rotations, MUX pairs, and the
-levels of a 16-bit unit run by the netlist engine.
+across gate tiles of 128 with ragged tails, K splits of 8, 4, 3 and 1 (the
+launcher's choice for 1, 2, 3 and 10 tiles; 19 tiles run unsplit), zero
+rotations, MUX pairs, and the levels of a 16-bit unit run by the netlist
+engine.
 """
 import numpy as np
 import pytest
@@ -152,3 +153,22 @@ def test_form_rejects_bad_values(ce, ctx):
     for bad in (-1, 2):
         with pytest.raises(Exception):
             ce.ce_set_external_product_form(c, bad)
+
+
+def test_profile_times_the_mma_launches(ce, ctx):
+    """Profiling kind 3: one event pair per CMux step's MMA launch."""
+    c, _ = ctx
+    rng = np.random.default_rng(71)
+    n = 40
+    a, b = random_ciphertexts(rng, n), random_ciphertexts(rng, n)
+    ce.ce_set_external_product_form(c, 1)
+    try:
+        ce.ce_profile_enable(c, True)
+        run_gates_device(ce, ctx, np.zeros(n, np.int64), a, b)
+        prof = ce.ce_profile_read(c)
+    finally:
+        ce.ce_profile_enable(c, False)
+        ce.ce_set_external_product_form(c, 0)
+    ms, cnt = prof["external_product_mma"]
+    assert cnt == 500
+    assert 0 < ms <= prof["blind_rotate"][0]

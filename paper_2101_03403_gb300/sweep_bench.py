@@ -2,6 +2,7 @@
 
   python -m paper_2101_03403_gb300.sweep_bench [--programs 32] [--reps 5]
   python -m paper_2101_03403_gb300.sweep_bench --xp-gates 2432
+  python -m paper_2101_03403_gb300.sweep_bench --forms-sweep
 
 * gate batches: bootstrapped gates/s and batch latency for batch sizes from
   one gate to 9728 (autotuned launch shape per size);
@@ -10,6 +11,10 @@
 * register programs: 32 encrypted programs (one per client, lengths uniform
   in [8, 64], ADD/SUB/AND/ORR/LSL/LSL_IMM/CMP/CSEL/MOV/MOV_IMM) advancing
   together through ce_exec_multi, and the longest one alone.
+
+With --forms-sweep: only the gate-batch sweep, once with the blind rotation's
+external products in the transform form (CUDA cores, autotuned shape) and
+once in the Toeplitz form (tensor cores).
 
 With --xp-gates N: one batch of N gates with the blind rotation's external
 products on the tensor cores (Toeplitz form), after one warm-up batch that
@@ -75,6 +80,7 @@ def main():
     ap.add_argument("--programs", type=int, default=32)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--xp-gates", type=int, default=0)
+    ap.add_argument("--forms-sweep", action="store_true")
     args = ap.parse_args()
     if args.xp_gates:
         return tensor_form_batch(args.xp_gates)
@@ -110,16 +116,26 @@ def main():
     out = {"gpu": torch.cuda.get_device_name(0)}
 
     # gate batches
-    sweep = []
-    for n in BATCHES:
-        a, b = rand_ct((n,)), rand_ct((n,))
-        ops = torch.from_numpy(rng.integers(0, 10, n).astype(np.uint8)).to(dev)
-        o = torch.empty((n, 501), dtype=torch.int32, device=dev)
-        ts = ev_time(lambda: ce.ce_gates_batch_device(ctx, cid, ops, a, b, o, n, stream),
-                     args.reps)
-        ms = pct(ts, 50)
-        sweep.append({"gates": n, "ms_p50": ms, "gates_per_s": n / ms * 1e3})
-    out["gate_batch_sweep"] = sweep
+    def batch_sweep():
+        sweep = []
+        for n in BATCHES:
+            a, b = rand_ct((n,)), rand_ct((n,))
+            ops = torch.from_numpy(rng.integers(0, 10, n).astype(np.uint8)).to(dev)
+            o = torch.empty((n, 501), dtype=torch.int32, device=dev)
+            ts = ev_time(lambda: ce.ce_gates_batch_device(ctx, cid, ops, a, b, o, n, stream),
+                         args.reps)
+            ms = pct(ts, 50)
+            sweep.append({"gates": n, "ms_p50": ms, "gates_per_s": n / ms * 1e3})
+        return sweep
+
+    out["gate_batch_sweep"] = batch_sweep()
+    if args.forms_sweep:
+        ce.ce_set_external_product_form(ctx, 1)
+        out["gate_batch_sweep_tensor_form"] = batch_sweep()
+        ce.ce_set_external_product_form(ctx, 0)
+        print(json.dumps(out), flush=True)
+        ctx.close()
+        return
 
     # functional units
     units = {}

@@ -172,3 +172,68 @@ def test_profile_times_the_mma_launches(ce, ctx):
     ms, cnt = prof["external_product_mma"]
     assert cnt == 500
     assert 0 < ms <= prof["blind_rotate"][0]
+
+
+def test_tensor_key_over_budget_is_refused(ce, keys):
+    """The tensor form's key (783,360,000 B) is built on first use and counted
+    against the HBM budget: a context with room for the client but not for
+    that key refuses with CE_EADMIT and keeps working in the transform form."""
+    import torch
+    from paper_2101_03403_gb300 import CeError
+    sk, ck = keys
+    c = ce.ce_create(0, ce.ce_client_footprint_bytes() + (100 << 20))
+    try:
+        cid = ce.ce_client_admit(c, ck)
+        rng = np.random.default_rng(80)
+        n = 3
+        a, b = random_ciphertexts(rng, n), random_ciphertexts(rng, n)
+        ops = np.array([0, 1, 2], np.uint8)
+        ce.ce_set_external_product_form(c, 1)
+        out = torch.empty((n, 501), dtype=torch.int32, device="cuda")
+        with pytest.raises(CeError) as ex:
+            ce.ce_gates_batch_device(c, cid, to_dev(ops), to_dev(a.view(np.int32)),
+                                     to_dev(b.view(np.int32)), out, n)
+        assert ex.value.code == -3                      # CE_EADMIT
+        ce.ce_set_external_product_form(c, 0)
+        ce.ce_gates_batch_device(c, cid, to_dev(ops), to_dev(a.view(np.int32)),
+                                 to_dev(b.view(np.int32)), out, n)
+        ce.ce_synchronize(c)
+        assert out.cpu().numpy().view(np.uint32).shape == (n, 501)
+    finally:
+        c.close()
+
+
+def test_programs_of_two_clients_in_tensor_form(ce, ctx, keys):
+    """Engine ticks that mix clients run the transform form (each gate group
+    with its own key); single-client ticks the tensor form: the registers
+    after the programs are identical to a run entirely in the transform form."""
+    c, cid = ctx
+    sk, ck = keys
+    sk2 = ce.ce_secret_keygen(777)
+    cid2 = ce.ce_client_admit(c, ce.ce_cloud_keygen(sk2, 777))
+    try:
+        rng = np.random.default_rng(81)
+        regs = {}
+        for cl, key in ((cid, sk), (cid2, sk2)):
+            for r in range(3):
+                v = int(rng.integers(0, 1 << 16))
+                bits = [ce.ce_encrypt_bit(key, (v >> j) & 1, 90 + r, cl * 16 + j)
+                        for j in range(16)]
+                regs[(cl, r)] = np.stack(bits)
+        progs = [[ce.insn("ADD", 2, 0, 1), ce.insn("AND", 0, 2, 1)],
+                 [ce.insn("SUB", 2, 1, 0)]]
+        results = []
+        for form in (1, 0):
+            for (cl, r), v in regs.items():
+                ce.ce_reg_write(c, cl, r, v)
+            ce.ce_set_external_product_form(c, form)
+            try:
+                ce.ce_exec_multi(c, [cid, cid2], progs)
+                ce.ce_synchronize(c)
+            finally:
+                ce.ce_set_external_product_form(c, 0)
+            results.append([ce.ce_reg_read(c, cl, r) for cl in (cid, cid2) for r in range(3)])
+        for x, y in zip(*results):
+            assert (x == y).all()
+    finally:
+        ce.ce_client_evict(c, cid2)

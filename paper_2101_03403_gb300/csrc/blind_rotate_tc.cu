@@ -46,25 +46,25 @@ namespace {
 
 constexpr int kTtM = 128;                             // gates per tile (MMA M)
 constexpr int kTtN = 128;                             // output coefficients per tile (MMA N)
-constexpr int kTtKC = 64;                             // K per pipeline chunk
+constexpr int kTtKC = 256;                            // K per pipeline chunk
 constexpr int kTtRows = 2 * kGadgetL;                 // six digit polynomials
-constexpr int kTtChunks = kTtRows * kRingN / kTtKC;   // 96 chunks per sweep
-constexpr int kTtChunksPerRow = kRingN / kTtKC;       // 16
+constexpr int kTtChunks = kTtRows * kRingN / kTtKC;   // 24 chunks per sweep
+constexpr int kTtChunksPerRow = kRingN / kTtKC;       // 4
 constexpr int kTtCoefTiles = 2 * kRingN / kTtN;       // 16
 constexpr int kTtLimbs = 4;                           // key limbs
 constexpr int kTtQ = 2 * kRingN / 8 - 1;              // 255 core matrices per sequence
-constexpr int kTtSlots = 6;
-constexpr int kTtABytes = kTtM * kTtKC * 2;           // 16,384: digit operand of a chunk
-constexpr int kTtBBlocks = kTtN / 8 + kTtKC / 8 - 1;  // 23 core matrices per key limb
-constexpr int kTtBLimbBytes = kTtBBlocks * 128;       // 2,944
-constexpr int kTtStage = kTtABytes + kTtLimbs * kTtBLimbBytes;  // 28,160
-constexpr int kTtASbo = (kTtKC / 8) * 128;            // 1,024: 8-row groups of the digits
+constexpr int kTtSlots = 2;
+constexpr int kTtABytes = kTtM * kTtKC * 2;           // 65,536: digit operand of a chunk
+constexpr int kTtBBlocks = kTtN / 8 + kTtKC / 8 - 1;  // 47 core matrices per key limb
+constexpr int kTtBLimbBytes = kTtBBlocks * 128;       // 6,016
+constexpr int kTtStage = kTtABytes + kTtLimbs * kTtBLimbBytes;  // 89,600
+constexpr int kTtASbo = (kTtKC / 8) * 128;            // 4,096: 8-row groups of the digits
 constexpr uint32_t kTtTmemCols = 512;
 constexpr uint32_t kDecompOffset = 0x80200802u;       // as in the transform path
 
 static_assert(kTtLimbs * kTtN <= int(kTtTmemCols), "four accumulators fit in TMEM");
 static_assert(kTtStage % 128 == 0 && kTtBLimbBytes % 16 == 0, "bulk copies stay 16-byte aligned");
-// The highest core matrix a chunk reads: q0 + 22 with q0 = (n0 + k0) / 8.
+// The highest core matrix a chunk reads: q0 + 46 with q0 = (n0 + k0) / 8.
 static_assert((kRingN - kTtN + kRingN - kTtKC) / 8 + kTtBBlocks - 1 < kTtQ, "Hankel range");
 
 struct TtSmem {
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) tt_init_kernel(const uint16_t *__restrict
 // Block: 8 gates (one 8-row group of the digit operand), 256 threads.  Digit
 // p of coefficient n of half c of D = X^abar_i ACC - ACC goes to K index
 // (c*3 + p)*N + (N - 1 - n), split into a low and a high 5-bit limb; limb b
-// of gate tile T, chunk ch is one contiguous 16 KB block of 16 x 8 core
+// of gate tile T, chunk ch is one contiguous 64 KB block of 16 x 32 core
 // matrices (gates x K).  Gates beyond n_jobs get zero digits.
 __global__ void __launch_bounds__(256) tt_digits_kernel(const uint32_t *__restrict__ acc,
                                                         const uint16_t *__restrict__ abar,
@@ -209,11 +209,13 @@ __global__ void __launch_bounds__(256) tt_digits_kernel(const uint32_t *__restri
     }
 #pragma unroll
     for (int p = 0; p < kGadgetL; ++p) {
-      const int ch = (c * kGadgetL + p) * kTtChunksPerRow + k8 / 8, C = k8 % 8;
+      constexpr int kCm = kTtKC / 8;  // core matrices along K in a chunk
+      const int ch = (c * kGadgetL + p) * kTtChunksPerRow + k8 / kCm, C = k8 % kCm;
 #pragma unroll
       for (int b = 0; b < 2; ++b) {
         const size_t off =
-            ((((size_t(b) * n_tiles + T) * kTtChunks + ch) * (kTtM / 8) + R) * 8 + C) * 64 + gi * 8;
+            ((((size_t(b) * n_tiles + T) * kTtChunks + ch) * (kTtM / 8) + R) * kCm + C) * 64 +
+            gi * 8;
         const uint32_t(&v)[4] = b ? hi[p] : lo[p];
         *reinterpret_cast<uint4 *>(digits + off) = make_uint4(v[0], v[1], v[2], v[3]);
       }
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(192, 1) tt_mma_kernel(const uint16_t *__restri
 
   if (warp == 4 && lane == 0) {
     // Producer: chunk c = sweep * nch + local chunk; digits of limb `sweep`,
-    // key sequences of digit row r = ch / 16 starting at q0 = (n0 + k0) / 8.
+    // key sequences of digit row r = ch / 4 starting at q0 = (n0 + k0) / 8.
     for (int c = 0; c < total; ++c) {
       const int slot = c % kTtSlots;
       if (c >= kTtSlots &&
@@ -302,7 +304,7 @@ __global__ void __launch_bounds__(192, 1) tt_mma_kernel(const uint16_t *__restri
       *n_issued = c + 1;
     }
   } else if (warp == 5 && lane == 0) {
-    // MMA issuer: per chunk 4 K-steps x 4 key limbs; accumulators restart at
+    // MMA issuer: per chunk 16 K-steps x 4 key limbs; accumulators restart at
     // each sweep, whose first MMA waits until the epilogue has read TMEM.
     for (int c = 0; c < total; ++c) {
       const int slot = c % kTtSlots;
@@ -434,7 +436,7 @@ cudaError_t launch_bsk_to_hankel(const uint32_t *bsk, uint16_t *hankel, cudaStre
   return cudaGetLastError();
 }
 
-// K split of a launch: the split k (a divisor of the 96 chunks) with the
+// K split of a launch: the split k (a divisor of the 24 chunks) with the
 // least modelled time, waves(k) x (1/k + 0.12 [k > 1]) in units of one
 // CTA's full-K work: waves(k) = ceil(16 tiles k / sms), and 0.12 is the
 // measured extra cost of a CTA whose partial sums go through atomics.

@@ -29,6 +29,8 @@
 // output coefficients (N) with the four key limbs in four accumulators (the
 // whole 512-column TMEM), in two sweeps over K (low digit limb, then high),
 // each followed by an epilogue that recombines the limbs and adds into ACC.
+// K streams in chunks of 256 through a two-slot ring: a chunk boundary (the
+// barrier wait and commit) costs about as much as 7 MMAs, so wide chunks win.
 // Every wait is bounded (2 s on %globaltimer, then an error flag and an
 // orderly exit).
 #include <cuda_fp16.h>

@@ -4,7 +4,9 @@ TEST INFRASTRUCTURE ONLY (see oracle.py).  Written from the paper's unit
 descriptions — §5 "Adder" (three-stage parallel-prefix adder, the span
 operator of Stage 2, Kogge-Stone levels of 15/14/12/8 operators for 16 bits),
 §5 "Subtractor" (a + NOT b + 1, the extra OR at bit 0), §5 "Shifter" (barrel
-shifter of log2(w) MUX stages), §5 "Multiplier" (read as an array multiplier
+shifter of log2(w) MUX stages; the right shifts as the same barrel with the
+bit order of input and output reversed, the arithmetic one shifting in the
+MSB), §5 "Multiplier" (read as an array multiplier
 keeping the low w bits), §5 "Divider" (non-restoring division, add/subtract
 chosen by the sign of the partial remainder), §5 "Bitwise operations",
 §6 "Conditional Flags" (N, Z by an OR tree, C, V by the formula given there)
@@ -23,7 +25,8 @@ TRUE = (-1, True)
 MUX = 10
 OPS = {"NAND": 0, "AND": 1, "OR": 2, "XOR": 3, "NOR": 4, "XNOR": 5, "ANDNY": 6, "ANDYN": 7,
        "ORNY": 8, "ORYN": 9}
-UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "CSEL"]
+UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "CSEL", "LSR",
+         "ASR"]
 CONDS = ["EQ", "NE", "CS", "CC", "MI", "PL", "VS", "VC", "HI", "LS", "GE", "LT", "GT", "LE"]
 
 
@@ -175,6 +178,17 @@ def build(unit: str, w: int = 16, cond: int = 0) -> Net:
             k += 1
             sh *= 2
         out = x
+    elif unit in ("LSR", "ASR"):
+        # §5 "Logic right shift/Arithmetic right shift": the LSL barrel on
+        # the bit-reversed operand, output reversed back; ARS fills with the
+        # MSB instead of zero.
+        fill = a[w - 1] if unit == "ASR" else FALSE
+        x, k, sh = list(reversed(a)), 0, 1
+        while sh < w:
+            x = [net.mux(b[k], x[j - sh] if j >= sh else fill, x[j]) for j in range(w)]
+            k += 1
+            sh *= 2
+        out = list(reversed(x))
     elif unit == "MUL":
         pp = [[net.g("AND", a[j], b[i]) for j in range(w - i)] for i in range(w)]
         S = list(pp[0])
@@ -273,6 +287,11 @@ def armv8(unit: str, a: int, b: int, w: int = 16, cond: int = 0, nzcv: int = 0):
         return a | b
     if unit == "LSL":
         return (a << (b % w)) & m
+    if unit == "LSR":
+        return a >> (b % w)
+    if unit == "ASR":
+        sa = a - (1 << w) if a >> (w - 1) else a
+        return (sa >> (b % w)) & m
     if unit == "MUL":
         return (a * b) & m
     if unit == "UDIV":

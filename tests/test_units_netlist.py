@@ -7,7 +7,7 @@ import pytest
 
 from oracle import netlists as NL
 
-UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP"]
+UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "LSR", "ASR"]
 
 
 def eval_vec(net, inputs):
@@ -65,6 +65,52 @@ def test_random_width16(unit):
     b[40:80] = a[40:80]
     a[80:120] = 0xFFFF
     check_unit(unit, 16, a, b)
+
+
+@pytest.mark.parametrize("unit", UNITS)
+def test_random_width32(unit):
+    rng = np.random.default_rng(32)
+    n = 600 if unit == "UDIV" else 2000
+    a = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.int64)
+    b = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.int64)
+    b[:20] = 0
+    b[20:40] = a[20:40]
+    a[40:60] = 0xFFFFFFFF
+    b[60:120] = rng.integers(0, 64, 60)           # every shift amount mod 32
+    if unit == "UDIV":
+        b[120:200] = rng.integers(1, 1 << 16, 80)  # quotients of every size
+    check_unit(unit, 32, a, b)
+
+
+def test_right_shifts_are_the_reversed_left_shift():
+    """Independent of the ARMv8 model: LSR(a, s) = rev(LSL(rev(a), s)) and
+    ASR fills with the sign bit (brute force at width 8)."""
+    def rev(x):
+        return int(format(x, "08b")[::-1], 2)
+    a, s = np.meshgrid(np.arange(256), np.arange(8))
+    a, s = a.ravel(), s.ravel()
+    lsl = eval_vec(NL.build("LSL", 8), [(a >> i) & 1 for i in range(8)] + [(s >> i) & 1 for i in range(8)])
+    lsr = eval_vec(NL.build("LSR", 8), [(a >> i) & 1 for i in range(8)] + [(s >> i) & 1 for i in range(8)])
+    asr = eval_vec(NL.build("ASR", 8), [(a >> i) & 1 for i in range(8)] + [(s >> i) & 1 for i in range(8)])
+    val = lambda outs: sum(outs[i].astype(np.int64) << i for i in range(8))
+    revs = np.array([rev(int(x)) for x in range(256)])
+    # LSL on reversed operands, reversed back
+    lsl_rev = eval_vec(NL.build("LSL", 8), [(revs[a] >> i) & 1 for i in range(8)] +
+                       [(s >> i) & 1 for i in range(8)])
+    assert (val(lsr) == revs[val(lsl_rev)]).all()
+    sign = (a >> 7) & 1
+    fill = np.where(sign == 1, (0xFF << (8 - s)) & 0xFF, 0)
+    assert (val(asr) == (val(lsr) | fill)).all()
+    assert (val(lsl) == (a << s) & 0xFF).all()
+
+
+def test_right_shift_structure():
+    for unit in ("LSR", "ASR"):
+        for w, stages in ((16, 4), (32, 5)):
+            net = NL.build(unit, w)
+            # §5: log2(w) MUX stages of w MUXes (4 stages for 16 bits, 5 for 32)
+            assert net.depth == stages and len(net.gates) == stages * w
+            assert net.bootstraps == 2 * stages * w
 
 
 @pytest.mark.parametrize("cond", range(14))

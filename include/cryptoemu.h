@@ -237,7 +237,10 @@ typedef enum {
     CE_U_MUL = 6,         /* (a * b) mod 2^w, array multiplier (§5 "Multiplier") */
     CE_U_UDIV = 7,        /* a / b (0 for b = 0), non-restoring (§5 "Divider") */
     CE_U_CMP = 8,         /* NZCV flags of a - b (§6 "Conditional Flags") */
-    CE_U_CSEL = 9         /* cond(NZCV) ? rn : rm */
+    CE_U_CSEL = 9,        /* cond(NZCV) ? rn : rm */
+    CE_U_LSR = 10,        /* a >> (b mod w), the LSL barrel on the bit-reversed operand
+                             (§5 "Logic right shift/Arithmetic right shift") */
+    CE_U_ASR = 11         /* signed a >> (b mod w): as LSR, the MSB shifted in */
 } ce_unit;
 
 /* Shape of a unit's netlist for width w (a power of two, 2..32). */
@@ -259,6 +262,13 @@ ce_status ce_unit_netlist(int unit, int cond, int width, int32_t *buf, size_t ca
 ce_status ce_unit_eval_device(ce_ctx *ctx, int client, int unit, int cond,
                               const uint32_t *d_in, uint32_t *d_out, size_t n,
                               void *cuda_stream);
+/* The same at any width w (a power of two, 2..32; the paper's 32-bit units,
+ * §5): d_in [n][2w (CSEL: 2w + 4)][501], d_out [n][w (CMP: 4)][501].
+ * ce_unit_eval_device is this call with width 16.  CE_EINVAL for another
+ * width. */
+ce_status ce_unit_eval_device_width(ce_ctx *ctx, int client, int unit, int cond, int width,
+                                    const uint32_t *d_in, uint32_t *d_out, size_t n,
+                                    void *cuda_stream);
 /* Graph replay of ce_unit_eval_device on (1, default) or off (eager). */
 ce_status ce_set_unit_graphs(ce_ctx *ctx, int on);
 
@@ -280,7 +290,11 @@ typedef enum {
     CE_I_CMP = 8,      /* NZCV = flags(rn - rm) */
     CE_I_CSEL = 9,     /* rd = cond(NZCV) ? rn : rm (cond as for CE_U_CSEL) */
     CE_I_MOV = 10,     /* rd = rn (no bootstrap) */
-    CE_I_MOV_IMM = 11  /* rd = imm (8-bit, zero extended; trivial ciphertexts) */
+    CE_I_MOV_IMM = 11, /* rd = imm (8-bit, zero extended; trivial ciphertexts) */
+    CE_I_LSR = 12,     /* rd = rn >> (rm mod 16), logical (barrel shifter) */
+    CE_I_ASR = 13,     /* rd = rn >> (rm mod 16), arithmetic */
+    CE_I_LSR_IMM = 14, /* rd = rn >> (imm mod 16), logical (no bootstrap) */
+    CE_I_ASR_IMM = 15  /* rd = rn >> (imm mod 16), arithmetic (no bootstrap) */
 } ce_opcode;
 typedef struct { uint8_t op, rd, rn, rm, imm, cond; } ce_insn;
 
@@ -340,7 +354,9 @@ void ce_server_destroy(ce_server *s);
  * calls whose work overlaps on the GPU (different streams, different
  * contexts) race and corrupt each other's results, so serialise them.  No
  * scratch word needs to start at zero: each call writes everything it reads.
- * The keys are the client's keys held by the context (admitted earlier). */
+ * The keys are the client's keys held by the context (admitted earlier).
+ * It always uses the transform form of the external products and the
+ * CUDA-core key switch (whose scratch fits the fixed area). */
 ce_status ce_gates_batch_device_noalloc(ce_ctx *ctx, int client, const uint8_t *d_ops,
                                         const uint32_t *d_a, const uint32_t *d_b,
                                         uint32_t *d_out, size_t n, void *cuda_stream);

@@ -76,6 +76,7 @@ def lib() -> ctypes.CDLL:
                                ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "ce_unit_netlist": (i32, [i32, i32, i32, vp, sz, ctypes.POINTER(sz)]),
         "ce_unit_eval_device": (i32, [vp, i32, i32, i32, vp, vp, sz, vp]),
+        "ce_unit_eval_device_width": (i32, [vp, i32, i32, i32, i32, vp, vp, sz, vp]),
         "ce_set_unit_graphs": (i32, [vp, i32]),
         "ce_reg_write": (i32, [vp, i32, i32, vp]),
         "ce_reg_read": (i32, [vp, i32, i32, vp]),
@@ -342,7 +343,8 @@ def ce_profile_read(ctx: Context) -> dict:
     return {name: (ms[i], cnt[i]) for i, name in enumerate(KERNEL_KINDS)}
 
 
-UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "CSEL"]
+UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "CSEL", "LSR",
+         "ASR"]
 UNIT_ID = {u: i for i, u in enumerate(UNITS)}
 
 
@@ -381,7 +383,7 @@ def ce_unit_netlist(unit, cond: int = 0, width: int = 16) -> dict:
 
 
 OPCODES = ["ADD", "SUB", "AND", "ORR", "LSL", "LSL_IMM", "MUL", "UDIV", "CMP", "CSEL", "MOV",
-           "MOV_IMM"]
+           "MOV_IMM", "LSR", "ASR", "LSR_IMM", "ASR_IMM"]
 OPCODE_ID = {o: i for i, o in enumerate(OPCODES)}
 CONDS = ["EQ", "NE", "CS", "CC", "MI", "PL", "VS", "VC", "HI", "LS", "GE", "LT", "GT", "LE"]
 
@@ -401,6 +403,13 @@ def ce_unit_eval_device(ctx: Context, client: int, unit, d_in, d_out, n: int, co
                         stream=None):
     _check(lib().ce_unit_eval_device(ctx.ptr, client, _unit(unit), cond, _addr(d_in), _addr(d_out),
                                      n, _stream(stream)), "ce_unit_eval_device")
+
+
+def ce_unit_eval_device_width(ctx: Context, client: int, unit, width: int, d_in, d_out, n: int,
+                              cond: int = 0, stream=None):
+    _check(lib().ce_unit_eval_device_width(ctx.ptr, client, _unit(unit), cond, width, _addr(d_in),
+                                           _addr(d_out), n, _stream(stream)),
+           "ce_unit_eval_device_width")
 
 
 def ce_set_unit_graphs(ctx: Context, on: bool):

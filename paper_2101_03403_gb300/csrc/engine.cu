@@ -98,7 +98,7 @@ struct RegFile {
 };
 
 struct Plan {
-  int unit = 0, cond = 0, client = 0, xp = 0;
+  int unit = 0, cond = 0, width = 0, client = 0, xp = 0;
   size_t n = 0;
   const uint32_t *d_in = nullptr;
   uint32_t *d_out = nullptr;
@@ -192,12 +192,12 @@ class Engine {
     if (r.slot > kSlotSink && --rc[r.slot] == 0) free_.push_back(r.slot);
   }
 
-  const Netlist *netlist(int unit, int cond) {
-    const int key = unit * 16 + cond;
+  const Netlist *netlist(int unit, int cond, int width = kWidth) {
+    const int key = (width * 64 + unit) * 16 + cond;
     auto it = nets.find(key);
     if (it != nets.end()) return &it->second;
     Netlist n;
-    if (!build_unit(unit, kWidth, unit == kUnitCsel ? cond : 0, &n)) return nullptr;
+    if (!build_unit(unit, width, unit == kUnitCsel ? cond : 0, &n)) return nullptr;
     return &nets.emplace(key, std::move(n)).first->second;
   }
 
@@ -449,17 +449,17 @@ class Engine {
     p.slots.clear();
   }
 
-  ce_status make_plan(int unit, int cond, int client, size_t n, const uint32_t *d_in,
+  ce_status make_plan(int unit, int cond, int width, int client, size_t n, const uint32_t *d_in,
                       uint32_t *d_out, Plan **out) {
     for (auto &p : plans)
-      if (p->unit == unit && p->cond == cond && p->client == client && p->n == n &&
-          p->d_in == d_in && p->d_out == d_out && p->xp == ctx->cfg_xp) {
+      if (p->unit == unit && p->cond == cond && p->width == width && p->client == client &&
+          p->n == n && p->d_in == d_in && p->d_out == d_out && p->xp == ctx->cfg_xp) {
         p->last_use = ++use_clock;
         *out = p.get();
         return CE_OK;
       }
-    const Netlist *net = netlist(unit, cond);
-    if (!net) return set_error(CE_EINVAL, "engine: bad unit");
+    const Netlist *net = netlist(unit, cond, width);
+    if (!net) return set_error(CE_EINVAL, "engine: bad unit or width");
     if (plans.size() >= 8) {  // evict the least recently used plan
       auto lru = std::min_element(plans.begin(), plans.end(), [](const auto &a, const auto &b) {
         return a->last_use < b->last_use;
@@ -470,6 +470,7 @@ class Engine {
     auto p = std::make_unique<Plan>();
     p->unit = unit;
     p->cond = cond;
+    p->width = width;
     p->client = client;
     p->xp = ctx->cfg_xp;
     p->n = n;
@@ -577,10 +578,11 @@ class Engine {
     return CE_OK;
   }
 
-  ce_status eval_unit(int unit, int cond, int client, const uint32_t *d_in, uint32_t *d_out,
+  ce_status eval_unit(int unit, int cond, int width, int client, const uint32_t *d_in,
+                      uint32_t *d_out,
                       size_t n, cudaStream_t st, int *launches) {
     Plan *p;
-    ce_status s = make_plan(unit, cond, client, n, d_in, d_out, &p);
+    ce_status s = make_plan(unit, cond, width, client, n, d_in, d_out, &p);
     if (s != CE_OK) return s;
     if (!use_graphs || ctx->profile) return run_plan(*p, st, launches);
     s = ensure_job_scratch(ctx, p->max_jobs);
@@ -664,7 +666,8 @@ bool live_client(ce_ctx *ctx, int client) {
 // Instruction set (16-bit registers R0..R7, encrypted NZCV).
 enum Opcode : uint8_t {
   kAdd = 0, kSub = 1, kAnd = 2, kOrr = 3, kLsl = 4, kLslImm = 5, kMul = 6, kUdiv = 7,
-  kCmp = 8, kCsel = 9, kMov = 10, kMovImm = 11, kOpcodes = 12
+  kCmp = 8, kCsel = 9, kMov = 10, kMovImm = 11, kLsr = 12, kAsr = 13, kLsrImm = 14,
+  kAsrImm = 15, kOpcodes = 16
 };
 
 int unit_of(uint8_t op) {
@@ -678,6 +681,8 @@ int unit_of(uint8_t op) {
     case kUdiv: return kUnitUdiv;
     case kCmp: return kUnitCmp;
     case kCsel: return kUnitCsel;
+    case kLsr: return kUnitLsr;
+    case kAsr: return kUnitAsr;
     default: return -1;
   }
 }
@@ -701,15 +706,18 @@ ce_status advance(Engine &E, Run &r) {
     const ce_insn &I = r.code[r.pc];
     if (I.op >= kOpcodes || I.rd >= kRegs || I.rn >= kRegs || I.rm >= kRegs || I.cond > 13)
       return set_error(CE_EINVAL, "ce_exec: malformed instruction at index " + std::to_string(r.pc));
-    if (I.op == kLslImm || I.op == kMov || I.op == kMovImm) {
+    if (I.op == kLslImm || I.op == kLsrImm || I.op == kAsrImm || I.op == kMov ||
+        I.op == kMovImm) {
+      // shifts by a constant only move wires (§5: no bootstrapping)
       SRef nv[kWidth];
+      const int sh = I.imm % kWidth;
+      const SRef msb = R.r[I.rn][kWidth - 1];
       for (int j = 0; j < kWidth; ++j) {
         if (I.op == kMov) nv[j] = R.r[I.rn][j];
         else if (I.op == kMovImm) nv[j] = SRef{kSlotFalse, bool((I.imm >> j) & 1)};
-        else {
-          const int sh = I.imm % kWidth;
-          nv[j] = j >= sh ? R.r[I.rn][j - sh] : SRef{kSlotFalse, false};
-        }
+        else if (I.op == kLslImm) nv[j] = j >= sh ? R.r[I.rn][j - sh] : SRef{kSlotFalse, false};
+        else if (j + sh < kWidth) nv[j] = R.r[I.rn][j + sh];
+        else nv[j] = I.op == kAsrImm ? msb : SRef{kSlotFalse, false};
         E.ref(nv[j]);
       }
       for (int j = 0; j < kWidth; ++j) {
@@ -878,12 +886,14 @@ ce_status exec_programs(ce_ctx *ctx, size_t n_prog, const int *clients, const ce
 
 using namespace ce;
 
-extern "C" ce_status ce_unit_eval_device(ce_ctx *ctx, int client, int unit, int cond,
-                                         const uint32_t *d_in, uint32_t *d_out, size_t n,
-                                         void *cuda_stream) {
+extern "C" ce_status ce_unit_eval_device_width(ce_ctx *ctx, int client, int unit, int cond,
+                                               int width, const uint32_t *d_in, uint32_t *d_out,
+                                               size_t n, void *cuda_stream) {
   if (!ctx) return set_error(CE_EINVAL, "ce_unit_eval_device: null context");
   if (unit < 0 || unit >= kUnitCount || cond < 0 || cond > 13)
     return set_error(CE_EINVAL, "ce_unit_eval_device: bad unit or condition");
+  if (width < 2 || width > 32 || (width & (width - 1)))
+    return set_error(CE_EINVAL, "ce_unit_eval_device: width must be a power of two in 2..32");
   if (!live_client(ctx, client)) return set_error(CE_ENOTFOUND, "ce_unit_eval_device: unknown client");
   if (n == 0) {
     ctx->last_launches = 0;
@@ -897,9 +907,15 @@ extern "C" ce_status ce_unit_eval_device(ce_ctx *ctx, int client, int unit, int 
   cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
   int launches = 0;
   std::lock_guard<std::recursive_mutex> lock(E->mu);
-  s = E->eval_unit(unit, cond, client, d_in, d_out, n, st, &launches);
+  s = E->eval_unit(unit, cond, width, client, d_in, d_out, n, st, &launches);
   ctx->last_launches = launches;
   return s;
+}
+
+extern "C" ce_status ce_unit_eval_device(ce_ctx *ctx, int client, int unit, int cond,
+                                         const uint32_t *d_in, uint32_t *d_out, size_t n,
+                                         void *cuda_stream) {
+  return ce_unit_eval_device_width(ctx, client, unit, cond, 16, d_in, d_out, n, cuda_stream);
 }
 
 extern "C" ce_status ce_set_unit_graphs(ce_ctx *ctx, int on) {

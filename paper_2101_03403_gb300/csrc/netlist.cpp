@@ -213,6 +213,21 @@ bool build_unit(int unit, int w, int cond, Netlist *out) {
       o = x;
       break;
     }
+    case kUnitLsr:
+    case kUnitAsr: {
+      // §5: the left-shift barrel on the operand in reversed bit order, the
+      // result reversed back; the arithmetic shift brings in the MSB where
+      // the logical one brings in zeros.
+      const Ref fill = unit == kUnitAsr ? a[w - 1] : constant(false);
+      std::vector<Ref> x(a.rbegin(), a.rend());
+      for (int k = 0, sh = 1; sh < w; ++k, sh *= 2) {
+        std::vector<Ref> y(w);
+        for (int j = 0; j < w; ++j) y[j] = B.mux(b[k], j >= sh ? x[j - sh] : fill, x[j]);
+        x = y;
+      }
+      o.assign(x.rbegin(), x.rend());
+      break;
+    }
     case kUnitMul: {
       // Array multiplier, low w bits: partial products pp[i][j] = a_j AND b_i
       // (i + j < w); row i (i >= 1) adds pp[i] into the running sum at

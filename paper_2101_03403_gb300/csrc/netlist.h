@@ -55,7 +55,9 @@ enum Unit : int {
   kUnitUdiv = 7,       // non-restoring divider (§5 "Divider"), x / 0 = 0
   kUnitCmp = 8,        // NZCV of a - b (§6 "Conditional Flags")
   kUnitCsel = 9,       // cond(NZCV) ? rn : rm, cond in 0..13 (EQ..LE)
-  kUnitCount = 10
+  kUnitLsr = 10,       // logical right shift, register amount (§5 "Logic right shift")
+  kUnitAsr = 11,       // arithmetic right shift (§5 "Arithmetic right shift")
+  kUnitCount = 12
 };
 
 // Inputs: a[width] then b[width] (CSEL: rn[width], rm[width], N, Z, C, V).

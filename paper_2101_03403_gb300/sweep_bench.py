@@ -3,6 +3,7 @@
   python -m paper_2101_03403_gb300.sweep_bench [--programs 32] [--reps 5]
   python -m paper_2101_03403_gb300.sweep_bench --xp-gates 2432
   python -m paper_2101_03403_gb300.sweep_bench --forms-sweep
+  python -m paper_2101_03403_gb300.sweep_bench --width 32
 
 * gate batches: bootstrapped gates/s and batch latency for batch sizes from
   one gate to 9728 (autotuned launch shape per size);
@@ -11,6 +12,9 @@
 * register programs: 32 encrypted programs (one per client, lengths uniform
   in [8, 64], ADD/SUB/AND/ORR/LSL/LSL_IMM/CMP/CSEL/MOV/MOV_IMM) advancing
   together through ce_exec_multi, and the longest one alone.
+
+With --width W (W != 16): only the functional units at width W, latency of
+1 and of 16 operand sets (UDIV: 1).
 
 With --forms-sweep: only the gate-batch sweep, once with the blind rotation's
 external products in the transform form (CUDA cores, autotuned shape) and
@@ -81,6 +85,7 @@ def main():
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--xp-gates", type=int, default=0)
     ap.add_argument("--forms-sweep", action="store_true")
+    ap.add_argument("--width", type=int, default=16)
     args = ap.parse_args()
     if args.xp_gates:
         return tensor_form_batch(args.xp_gates)
@@ -127,6 +132,25 @@ def main():
             ms = pct(ts, 50)
             sweep.append({"gates": n, "ms_p50": ms, "gates_per_s": n / ms * 1e3})
         return sweep
+
+    if args.width != 16:
+        units = {}
+        for unit in ce.UNITS:
+            info = ce.ce_unit_info(unit, 0, args.width)
+            row = {"bootstraps_per_op": info["n_bootstraps"], "depth": info["depth"]}
+            for n in ((1,) if unit == "UDIV" else (1, 16)):
+                d_in = rand_ct((n, info["n_inputs"]))
+                d_out = torch.empty((n, info["n_outputs"], 501), dtype=torch.int32, device=dev)
+                ts = ev_time(lambda: ce.ce_unit_eval_device_width(ctx, cid, unit, args.width, d_in,
+                                                                  d_out, n, 0, stream),
+                             min(args.reps, 3))
+                row[f"n{n}"] = {"p50_ms": pct(ts, 50), "p99_ms": pct(ts, 99),
+                                "bootstraps_per_s": n * info["n_bootstraps"] / pct(ts, 50) * 1e3}
+            units[unit] = row
+        out[f"unit_latency_width{args.width}"] = units
+        print(json.dumps(out), flush=True)
+        ctx.close()
+        return
 
     out["gate_batch_sweep"] = batch_sweep()
     if args.forms_sweep:

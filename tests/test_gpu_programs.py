@@ -23,6 +23,8 @@ def run_plain(prog, regs, nzcv=0):
             regs[rd] = NL.armv8("CSEL", a, b, W, cond, nzcv)
         elif op == "LSL_IMM":
             regs[rd] = (a << (imm % W)) & M
+        elif op in ("LSR_IMM", "ASR_IMM"):
+            regs[rd] = NL.armv8(op[:3], a, imm % W, W)
         elif op == "MOV":
             regs[rd] = a
         elif op == "MOV_IMM":
@@ -33,7 +35,8 @@ def run_plain(prog, regs, nzcv=0):
 
 
 def random_program(rng, length):
-    ops = ["ADD", "SUB", "AND", "ORR", "LSL", "LSL_IMM", "CMP", "CSEL", "MOV", "MOV_IMM"]
+    ops = ["ADD", "SUB", "AND", "ORR", "LSL", "LSL_IMM", "CMP", "CSEL", "MOV", "MOV_IMM", "LSR",
+           "ASR", "LSR_IMM", "ASR_IMM"]
     prog = [("CMP", 0, 1, 2, 0, 0)]           # flags defined before any CSEL
     while len(prog) < length:
         op = ops[rng.integers(len(ops))]

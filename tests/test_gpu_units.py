@@ -55,7 +55,8 @@ def operands(rng, n):
     return a, b
 
 
-@pytest.mark.parametrize("unit", ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "CMP"])
+@pytest.mark.parametrize("unit", ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "CMP",
+                                  "LSR", "ASR"])
 def test_unit_semantics(ce, ctx, keys, unit):
     sk, _ = keys
     rng = np.random.default_rng(hash(unit) % 1000)
@@ -111,12 +112,12 @@ def test_graph_replay_equals_eager(ce, ctx, keys):
     assert (g1 == g2).all() and (g1 == eager).all()
 
 
-@pytest.mark.parametrize("unit", ["AND", "LSL", "ADD"])
+@pytest.mark.parametrize("unit", ["AND", "LSL", "ADD", "ASR"])
 def test_unit_ciphertexts_match_oracle(ce, ctx, keys, O, full_keys, unit):
     """One instance, every output word equal to the oracle evaluating its own
     (independently built) netlist gate by gate."""
     sk, _ = keys
-    a, b = np.array([0xBEEF]), np.array([0x0137 if unit != "LSL" else 5])
+    a, b = np.array([0xBEEF]), np.array([5 if unit in ("LSL", "ASR") else 0x0137])
     inp = enc_operands(ce, sk, operand_bits(a, b), 11)
     got = run_unit(ce, ctx, unit, inp, W)[0]
     net = NL.build(unit, W)

@@ -149,7 +149,7 @@ def lib():
 
 
 @pytest.mark.parametrize("unit", UNITS + ["CSEL"])
-@pytest.mark.parametrize("w", [8, 16])
+@pytest.mark.parametrize("w", [8, 16, 32])
 def test_library_netlist_equals_oracle(lib, unit, w):
     conds = range(14) if unit == "CSEL" else [0]
     for cond in conds:

@@ -240,7 +240,9 @@ typedef enum {
     CE_U_CSEL = 9,        /* cond(NZCV) ? rn : rm */
     CE_U_LSR = 10,        /* a >> (b mod w), the LSL barrel on the bit-reversed operand
                              (§5 "Logic right shift/Arithmetic right shift") */
-    CE_U_ASR = 11         /* signed a >> (b mod w): as LSR, the MSB shifted in */
+    CE_U_ASR = 11,        /* signed a >> (b mod w): as LSR, the MSB shifted in */
+    CE_U_EOR = 12,        /* bitwise XOR (§5 "Bitwise operations") */
+    CE_U_ORN = 13         /* bitwise a OR NOT b */
 } ce_unit;
 
 /* Shape of a unit's netlist for width w (a power of two, 2..32). */
@@ -294,7 +296,21 @@ typedef enum {
     CE_I_LSR = 12,     /* rd = rn >> (rm mod 16), logical (barrel shifter) */
     CE_I_ASR = 13,     /* rd = rn >> (rm mod 16), arithmetic */
     CE_I_LSR_IMM = 14, /* rd = rn >> (imm mod 16), logical (no bootstrap) */
-    CE_I_ASR_IMM = 15  /* rd = rn >> (imm mod 16), arithmetic (no bootstrap) */
+    CE_I_ASR_IMM = 15, /* rd = rn >> (imm mod 16), arithmetic (no bootstrap) */
+    CE_I_EOR = 16,     /* rd = rn ^ rm */
+    CE_I_ORN = 17,     /* rd = rn | ~rm */
+    /* §5 "Bitwise operations" with an immediate and NOT, and "Data movement":
+     * no bootstrap (wire copies, negations and constants).  imm: 8 bits, zero
+     * extended; BFC/BFI: field lsb = imm & 15, width = (imm >> 4) + 1, clipped
+     * at bit 15. */
+    CE_I_MVN = 18,     /* rd = ~rn */
+    CE_I_AND_IMM = 19, /* rd = rn & imm */
+    CE_I_ORR_IMM = 20, /* rd = rn | imm */
+    CE_I_EOR_IMM = 21, /* rd = rn ^ imm */
+    CE_I_BFC = 22,     /* clear bits [lsb, lsb + width) of rd */
+    CE_I_BFI = 23,     /* rd[lsb, lsb + width) = rn[0, width) */
+    CE_I_RBIT = 24,    /* rd = rn with the bit order reversed */
+    CE_I_REV = 25      /* rd = rn with the two bytes swapped */
 } ce_opcode;
 typedef struct { uint8_t op, rd, rn, rm, imm, cond; } ce_insn;
 

@@ -26,7 +26,7 @@ MUX = 10
 OPS = {"NAND": 0, "AND": 1, "OR": 2, "XOR": 3, "NOR": 4, "XNOR": 5, "ANDNY": 6, "ANDYN": 7,
        "ORNY": 8, "ORYN": 9}
 UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "CSEL", "LSR",
-         "ASR"]
+         "ASR", "EOR", "ORN"]
 CONDS = ["EQ", "NE", "CS", "CC", "MI", "PL", "VS", "VC", "HI", "LS", "GE", "LT", "GT", "LE"]
 
 
@@ -171,6 +171,10 @@ def build(unit: str, w: int = 16, cond: int = 0) -> Net:
         out, _ = prefix_adder(net, a, [neg(x) for x in b], "one")
     elif unit in ("AND", "ORR"):
         out = [net.g("AND" if unit == "AND" else "OR", a[i], b[i]) for i in range(w)]
+    elif unit == "EOR":
+        out = [net.g("XOR", a[i], b[i]) for i in range(w)]
+    elif unit == "ORN":                     # a OR NOT b: the ORYN gate per bit
+        out = [net.g("ORYN", a[i], b[i]) for i in range(w)]
     elif unit == "LSL":
         x, k, sh = list(a), 0, 1
         while sh < w:
@@ -285,6 +289,10 @@ def armv8(unit: str, a: int, b: int, w: int = 16, cond: int = 0, nzcv: int = 0):
         return a & b
     if unit == "ORR":
         return a | b
+    if unit == "EOR":
+        return a ^ b
+    if unit == "ORN":
+        return (a | ~b) & m
     if unit == "LSL":
         return (a << (b % w)) & m
     if unit == "LSR":
@@ -307,6 +315,41 @@ def armv8(unit: str, a: int, b: int, w: int = 16, cond: int = 0, nzcv: int = 0):
                  "LT": int(N != V), "GT": (1 - Z) & int(N == V), "LE": 1 - ((1 - Z) & int(N == V))}
         return a if table[CONDS[cond]] else b
     raise ValueError(unit)
+
+
+def armv8_insn(op: str, rd: int, rn: int, rm: int, imm: int, cond: int, nzcv: int,
+               w: int = 16):
+    """One register instruction of the emulated machine on plaintext values:
+    returns (new rd value, new nzcv).  §4 "Data Processing" and §5/§6 units;
+    imm is the 8-bit instruction immediate; BFC/BFI take lsb = imm & 15 and
+    width = (imm >> 4) + 1 (clipped at the register's top bit)."""
+    m = (1 << w) - 1
+    if op == "CMP":
+        N, Z, C, V = armv8("CMP", rn, rm, w)
+        return rd, N | Z << 1 | C << 2 | V << 3
+    if op == "CSEL":
+        return armv8("CSEL", rn, rm, w, cond, nzcv), nzcv
+    if op == "MOV":
+        return rn, nzcv
+    if op == "MOV_IMM":
+        return imm, nzcv
+    if op in ("LSL_IMM", "LSR_IMM", "ASR_IMM"):
+        return armv8(op[:3], rn, imm % w, w), nzcv
+    if op == "MVN":
+        return ~rn & m, nzcv
+    if op in ("AND_IMM", "ORR_IMM", "EOR_IMM"):
+        return armv8(op[:3], rn, imm, w), nzcv
+    lsb, width = imm & 15, (imm >> 4) + 1
+    field = ((1 << width) - 1) << lsb & m
+    if op == "BFC":
+        return rd & ~field & m, nzcv
+    if op == "BFI":
+        return (rd & ~field | (rn << lsb) & field) & m, nzcv
+    if op == "RBIT":
+        return from_bits(bits(rn, w)[::-1]), nzcv
+    if op == "REV":
+        return from_bits(sum((bits(rn, w)[8 * k:8 * k + 8] for k in reversed(range(w // 8))), [])), nzcv
+    return armv8(op, rn, rm, w), nzcv
 
 
 def eval_ciphertext(keys, net: Net, inputs):

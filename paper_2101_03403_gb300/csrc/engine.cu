@@ -667,8 +667,36 @@ bool live_client(ce_ctx *ctx, int client) {
 enum Opcode : uint8_t {
   kAdd = 0, kSub = 1, kAnd = 2, kOrr = 3, kLsl = 4, kLslImm = 5, kMul = 6, kUdiv = 7,
   kCmp = 8, kCsel = 9, kMov = 10, kMovImm = 11, kLsr = 12, kAsr = 13, kLsrImm = 14,
-  kAsrImm = 15, kOpcodes = 16
+  kAsrImm = 15, kEor = 16, kOrn = 17, kMvn = 18, kAndImm = 19, kOrrImm = 20, kEorImm = 21,
+  kBfc = 22, kBfi = 23, kRbit = 24, kRev = 25, kOpcodes = 26
 };
+
+// Instructions that only move, negate or fix wires (no bootstrap, §5 "Data
+// movement": TFHE's COPY/NOT/CONSTANT): the new value of bit j of rd.
+// Returns false for an instruction that needs gates.
+bool wire_move(const ce_insn &I, const SRef *rd, const SRef *rn, int j, SRef *out) {
+  const int sh = I.imm % kWidth;
+  const SRef fls{kSlotFalse, false}, tru{kSlotFalse, true};
+  const bool ib = (I.imm >> j) & 1;  // immediate bit (8-bit immediates: zero above bit 7)
+  const int lsb = I.imm & 15, width = (I.imm >> 4) + 1;  // BFC/BFI field
+  const bool in_field = j >= lsb && j < lsb + width;
+  switch (I.op) {
+    case kMov: *out = rn[j]; return true;
+    case kMovImm: *out = ib ? tru : fls; return true;
+    case kLslImm: *out = j >= sh ? rn[j - sh] : fls; return true;
+    case kLsrImm: *out = j + sh < kWidth ? rn[j + sh] : fls; return true;
+    case kAsrImm: *out = j + sh < kWidth ? rn[j + sh] : rn[kWidth - 1]; return true;
+    case kMvn: *out = SRef{rn[j].slot, !rn[j].neg}; return true;
+    case kAndImm: *out = ib ? rn[j] : fls; return true;
+    case kOrrImm: *out = ib ? tru : rn[j]; return true;
+    case kEorImm: *out = ib ? SRef{rn[j].slot, !rn[j].neg} : rn[j]; return true;
+    case kBfc: *out = in_field ? fls : rd[j]; return true;
+    case kBfi: *out = in_field ? rn[j - lsb] : rd[j]; return true;
+    case kRbit: *out = rn[kWidth - 1 - j]; return true;
+    case kRev: *out = rn[j ^ 8]; return true;  // byte swap of a 16-bit register
+    default: return false;
+  }
+}
 
 int unit_of(uint8_t op) {
   switch (op) {
@@ -683,6 +711,8 @@ int unit_of(uint8_t op) {
     case kCsel: return kUnitCsel;
     case kLsr: return kUnitLsr;
     case kAsr: return kUnitAsr;
+    case kEor: return kUnitEor;
+    case kOrn: return kUnitOrn;
     default: return -1;
   }
 }
@@ -706,18 +736,11 @@ ce_status advance(Engine &E, Run &r) {
     const ce_insn &I = r.code[r.pc];
     if (I.op >= kOpcodes || I.rd >= kRegs || I.rn >= kRegs || I.rm >= kRegs || I.cond > 13)
       return set_error(CE_EINVAL, "ce_exec: malformed instruction at index " + std::to_string(r.pc));
-    if (I.op == kLslImm || I.op == kLsrImm || I.op == kAsrImm || I.op == kMov ||
-        I.op == kMovImm) {
-      // shifts by a constant only move wires (§5: no bootstrapping)
+    SRef probe;
+    if (wire_move(I, R.r[I.rd], R.r[I.rn], 0, &probe)) {
       SRef nv[kWidth];
-      const int sh = I.imm % kWidth;
-      const SRef msb = R.r[I.rn][kWidth - 1];
       for (int j = 0; j < kWidth; ++j) {
-        if (I.op == kMov) nv[j] = R.r[I.rn][j];
-        else if (I.op == kMovImm) nv[j] = SRef{kSlotFalse, bool((I.imm >> j) & 1)};
-        else if (I.op == kLslImm) nv[j] = j >= sh ? R.r[I.rn][j - sh] : SRef{kSlotFalse, false};
-        else if (j + sh < kWidth) nv[j] = R.r[I.rn][j + sh];
-        else nv[j] = I.op == kAsrImm ? msb : SRef{kSlotFalse, false};
+        wire_move(I, R.r[I.rd], R.r[I.rn], j, &nv[j]);
         E.ref(nv[j]);
       }
       for (int j = 0; j < kWidth; ++j) {

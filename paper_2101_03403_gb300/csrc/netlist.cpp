@@ -198,8 +198,12 @@ bool build_unit(int unit, int w, int cond, Netlist *out) {
     }
     case kUnitAnd:
     case kUnitOrr:
-      for (int i = 0; i < w; ++i) o.push_back(B.gate(unit == kUnitAnd ? AND : OR, a[i], b[i]));
+    case kUnitEor:
+    case kUnitOrn: {
+      const uint8_t op = unit == kUnitAnd ? AND : unit == kUnitOrr ? OR : unit == kUnitEor ? XOR : ORYN;
+      for (int i = 0; i < w; ++i) o.push_back(B.gate(op, a[i], b[i]));
       break;
+    }
     case kUnitLsl: {
       // Barrel shifter: stage k selects, per bit j, x_{j-2^k} (0 below 2^k)
       // when amount bit k is set; amount bits above log2(w) are ignored

@@ -57,7 +57,9 @@ enum Unit : int {
   kUnitCsel = 9,       // cond(NZCV) ? rn : rm, cond in 0..13 (EQ..LE)
   kUnitLsr = 10,       // logical right shift, register amount (§5 "Logic right shift")
   kUnitAsr = 11,       // arithmetic right shift (§5 "Arithmetic right shift")
-  kUnitCount = 12
+  kUnitEor = 12,       // bitwise XOR (§5 "Bitwise operations")
+  kUnitOrn = 13,       // bitwise a OR NOT b
+  kUnitCount = 14
 };
 
 // Inputs: a[width] then b[width] (CSEL: rn[width], rm[width], N, Z, C, V).

@@ -15,28 +15,14 @@ W, M = 16, 0xFFFF
 def run_plain(prog, regs, nzcv=0):
     regs = list(regs)
     for op, rd, rn, rm, imm, cond in prog:
-        a, b = regs[rn], regs[rm]
-        if op == "CMP":
-            N, Z, C, V = NL.armv8("CMP", a, b, W)
-            nzcv = N | Z << 1 | C << 2 | V << 3
-        elif op == "CSEL":
-            regs[rd] = NL.armv8("CSEL", a, b, W, cond, nzcv)
-        elif op == "LSL_IMM":
-            regs[rd] = (a << (imm % W)) & M
-        elif op in ("LSR_IMM", "ASR_IMM"):
-            regs[rd] = NL.armv8(op[:3], a, imm % W, W)
-        elif op == "MOV":
-            regs[rd] = a
-        elif op == "MOV_IMM":
-            regs[rd] = imm
-        else:
-            regs[rd] = NL.armv8(op, a, b, W)
+        regs[rd], nzcv = NL.armv8_insn(op, regs[rd], regs[rn], regs[rm], imm, cond, nzcv, W)
     return regs, nzcv
 
 
 def random_program(rng, length):
     ops = ["ADD", "SUB", "AND", "ORR", "LSL", "LSL_IMM", "CMP", "CSEL", "MOV", "MOV_IMM", "LSR",
-           "ASR", "LSR_IMM", "ASR_IMM"]
+           "ASR", "LSR_IMM", "ASR_IMM", "EOR", "ORN", "MVN", "AND_IMM", "ORR_IMM", "EOR_IMM",
+           "BFC", "BFI", "RBIT", "REV"]
     prog = [("CMP", 0, 1, 2, 0, 0)]           # flags defined before any CSEL
     while len(prog) < length:
         op = ops[rng.integers(len(ops))]
@@ -82,6 +68,26 @@ def test_programs_two_clients(ce, ctx, keys, second_client):
         assert read_regs(ce, c, cid_, sk_) == exp_regs
         flags = [ce.ce_decrypt_bit(sk_, x) for x in ce.ce_flags_read(c, cid_)]
         assert flags == [(exp_nzcv >> k) & 1 for k in range(4)]
+
+
+def test_every_instruction(ce, ctx, keys):
+    """Each of the machine's register instructions at least once, in a random
+    order with random operands, against the plaintext model."""
+    c, cid = ctx
+    sk, _ = keys
+    rng = np.random.default_rng(2022)
+    ops = [o for o in ce.OPCODES if o not in ("MUL", "UDIV")]   # those two: test below
+    prog = [("CMP", 0, 1, 2, 0, 0)]
+    for op in rng.permutation(ops + ops):
+        prog.append((str(op), int(rng.integers(8)), int(rng.integers(8)), int(rng.integers(8)),
+                     int(rng.integers(256)), int(rng.integers(14))))
+    init = [int(x) for x in rng.integers(0, 1 << W, 8)]
+    load_regs(ce, c, cid, sk, init, 43)
+    ce.ce_exec(c, cid, [ce.insn(*i) for i in prog])
+    exp_regs, exp_nzcv = run_plain(prog, init)
+    assert read_regs(ce, c, cid, sk) == exp_regs
+    flags = [ce.ce_decrypt_bit(sk, x) for x in ce.ce_flags_read(c, cid)]
+    assert flags == [(exp_nzcv >> k) & 1 for k in range(4)]
 
 
 def test_mul_udiv_program(ce, ctx, keys):

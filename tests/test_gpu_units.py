@@ -56,7 +56,7 @@ def operands(rng, n):
 
 
 @pytest.mark.parametrize("unit", ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "CMP",
-                                  "LSR", "ASR"])
+                                  "LSR", "ASR", "EOR", "ORN"])
 def test_unit_semantics(ce, ctx, keys, unit):
     sk, _ = keys
     rng = np.random.default_rng(hash(unit) % 1000)

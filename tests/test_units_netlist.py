@@ -7,7 +7,8 @@ import pytest
 
 from oracle import netlists as NL
 
-UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "LSR", "ASR"]
+UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "LSR", "ASR",
+         "EOR", "ORN"]
 
 
 def eval_vec(net, inputs):

@@ -225,7 +225,7 @@ int ce_last_launch_count(ce_ctx *ctx);
 /* Functional units of the emulator (§5 "Data Processing Units", §6
  * "Conditional Flags") as netlists of bootstrapped gates.  Inputs: a[w]
  * then b[w] (bit 0 first); CSEL: rn[w], rm[w], N, Z, C, V.  Outputs: w bits;
- * CMP: N, Z, C, V of a - b.  cond (CSEL only): 0 EQ, 1 NE, 2 CS, 3 CC, 4 MI,
+ * CMP: N, Z, C, V of a - b; ADDS/SUBS: w bits then N, Z, C, V.  cond (CSEL only): 0 EQ, 1 NE, 2 CS, 3 CC, 4 MI,
  * 5 PL, 6 VS, 7 VC, 8 HI, 9 LS, 10 GE, 11 LT, 12 GT, 13 LE. */
 typedef enum {
     CE_U_ADD = 0,         /* Kogge-Stone parallel-prefix adder (§5 "Adder") */
@@ -242,7 +242,9 @@ typedef enum {
                              (§5 "Logic right shift/Arithmetic right shift") */
     CE_U_ASR = 11,        /* signed a >> (b mod w): as LSR, the MSB shifted in */
     CE_U_EOR = 12,        /* bitwise XOR (§5 "Bitwise operations") */
-    CE_U_ORN = 13         /* bitwise a OR NOT b */
+    CE_U_ORN = 13,        /* bitwise a OR NOT b */
+    CE_U_ADDS = 14,       /* a + b then its N, Z, C, V (outputs w + 4) */
+    CE_U_SUBS = 15        /* a - b then its N, Z, C, V (CMP keeping the difference) */
 } ce_unit;
 
 /* Shape of a unit's netlist for width w (a power of two, 2..32). */
@@ -310,7 +312,9 @@ typedef enum {
     CE_I_BFC = 22,     /* clear bits [lsb, lsb + width) of rd */
     CE_I_BFI = 23,     /* rd[lsb, lsb + width) = rn[0, width) */
     CE_I_RBIT = 24,    /* rd = rn with the bit order reversed */
-    CE_I_REV = 25      /* rd = rn with the two bytes swapped */
+    CE_I_REV = 25,     /* rd = rn with the two bytes swapped */
+    CE_I_ADDS = 26,    /* rd = rn + rm, NZCV = its flags (§6 flag-setting form) */
+    CE_I_SUBS = 27     /* rd = rn - rm, NZCV = flags(rn - rm) */
 } ce_opcode;
 typedef struct { uint8_t op, rd, rn, rm, imm, cond; } ce_insn;
 

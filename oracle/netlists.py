@@ -26,7 +26,7 @@ MUX = 10
 OPS = {"NAND": 0, "AND": 1, "OR": 2, "XOR": 3, "NOR": 4, "XNOR": 5, "ANDNY": 6, "ANDYN": 7,
        "ORNY": 8, "ORYN": 9}
 UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "CSEL", "LSR",
-         "ASR", "EOR", "ORN"]
+         "ASR", "EOR", "ORN", "ADDS", "SUBS"]
 CONDS = ["EQ", "NE", "CS", "CC", "MI", "PL", "VS", "VC", "HI", "LS", "GE", "LT", "GT", "LE"]
 
 
@@ -227,7 +227,7 @@ def build(unit: str, w: int = 16, cond: int = 0) -> Net:
             Q[0] = neg(A[w])
         nonzero = or_reduce(net, b)
         out = [net.g("AND", Q[k], nonzero) for k in range(w)]
-    elif unit == "CMP":
+    elif unit in ("CMP", "SUBS"):
         s, carry = prefix_adder(net, a, [neg(x) for x in b], "one")
         N = s[w - 1]
         Z = neg(or_reduce(net, s))
@@ -236,7 +236,18 @@ def build(unit: str, w: int = 16, cond: int = 0) -> Net:
         y1 = net.g("ANDYN", a[w - 1], b[w - 1])
         y2 = net.g("ANDYN", y1, s[w - 1])
         V = net.g("OR", x2, y2)
-        out = [N, Z, carry, V]
+        out = ([] if unit == "CMP" else s) + [N, Z, carry, V]
+    elif unit == "ADDS":
+        # §6's flags on a + b: V = (!a !b s) + (a b !s) with the operands as given
+        s, carry = prefix_adder(net, a, b)
+        N = s[w - 1]
+        Z = neg(or_reduce(net, s))
+        x1 = net.g("NOR", a[w - 1], b[w - 1])
+        x2 = net.g("AND", x1, s[w - 1])
+        y1 = net.g("AND", a[w - 1], b[w - 1])
+        y2 = net.g("ANDYN", y1, s[w - 1])
+        V = net.g("OR", x2, y2)
+        out = s + [N, Z, carry, V]
     elif unit == "CSEL":
         N, Z, C, V = (net.inp(2 * w + i) for i in range(4))
         c = cond_bit(net, cond, N, Z, C, V)
@@ -308,6 +319,12 @@ def armv8(unit: str, a: int, b: int, w: int = 16, cond: int = 0, nzcv: int = 0):
         r = (a - b) & m
         sa, sb, sr = a >> (w - 1), b >> (w - 1), r >> (w - 1)
         return [sr, int(r == 0), int(a >= b), int(sa != sb and sr != sa)]
+    if unit == "SUBS":
+        return [(a - b) & m] + armv8("CMP", a, b, w)
+    if unit == "ADDS":
+        r = (a + b) & m
+        sa, sb, sr = a >> (w - 1), b >> (w - 1), r >> (w - 1)
+        return [r, sr, int(r == 0), int(a + b > m), int(sa == sb and sr != sa)]
     if unit == "CSEL":
         N, Z, C, V = (nzcv >> i & 1 for i in range(4))
         table = {"EQ": Z, "NE": 1 - Z, "CS": C, "CC": 1 - C, "MI": N, "PL": 1 - N, "VS": V,
@@ -329,6 +346,9 @@ def armv8_insn(op: str, rd: int, rn: int, rm: int, imm: int, cond: int, nzcv: in
         return rd, N | Z << 1 | C << 2 | V << 3
     if op == "CSEL":
         return armv8("CSEL", rn, rm, w, cond, nzcv), nzcv
+    if op in ("ADDS", "SUBS"):
+        r, N, Z, C, V = armv8(op, rn, rm, w)
+        return r, N | Z << 1 | C << 2 | V << 3
     if op == "MOV":
         return rn, nzcv
     if op == "MOV_IMM":

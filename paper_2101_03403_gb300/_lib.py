@@ -344,7 +344,7 @@ def ce_profile_read(ctx: Context) -> dict:
 
 
 UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "CSEL", "LSR",
-         "ASR", "EOR", "ORN"]
+         "ASR", "EOR", "ORN", "ADDS", "SUBS"]
 UNIT_ID = {u: i for i, u in enumerate(UNITS)}
 
 
@@ -384,7 +384,7 @@ def ce_unit_netlist(unit, cond: int = 0, width: int = 16) -> dict:
 
 OPCODES = ["ADD", "SUB", "AND", "ORR", "LSL", "LSL_IMM", "MUL", "UDIV", "CMP", "CSEL", "MOV",
            "MOV_IMM", "LSR", "ASR", "LSR_IMM", "ASR_IMM", "EOR", "ORN", "MVN", "AND_IMM", "ORR_IMM",
-           "EOR_IMM", "BFC", "BFI", "RBIT", "REV"]
+           "EOR_IMM", "BFC", "BFI", "RBIT", "REV", "ADDS", "SUBS"]
 OPCODE_ID = {o: i for i, o in enumerate(OPCODES)}
 CONDS = ["EQ", "NE", "CS", "CC", "MI", "PL", "VS", "VC", "HI", "LS", "GE", "LT", "GT", "LE"]
 

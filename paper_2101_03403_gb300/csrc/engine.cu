@@ -668,7 +668,7 @@ enum Opcode : uint8_t {
   kAdd = 0, kSub = 1, kAnd = 2, kOrr = 3, kLsl = 4, kLslImm = 5, kMul = 6, kUdiv = 7,
   kCmp = 8, kCsel = 9, kMov = 10, kMovImm = 11, kLsr = 12, kAsr = 13, kLsrImm = 14,
   kAsrImm = 15, kEor = 16, kOrn = 17, kMvn = 18, kAndImm = 19, kOrrImm = 20, kEorImm = 21,
-  kBfc = 22, kBfi = 23, kRbit = 24, kRev = 25, kOpcodes = 26
+  kBfc = 22, kBfi = 23, kRbit = 24, kRev = 25, kAdds = 26, kSubs = 27, kOpcodes = 28
 };
 
 // Instructions that only move, negate or fix wires (no bootstrap, §5 "Data
@@ -713,6 +713,8 @@ int unit_of(uint8_t op) {
     case kAsr: return kUnitAsr;
     case kEor: return kUnitEor;
     case kOrn: return kUnitOrn;
+    case kAdds: return kUnitAdds;
+    case kSubs: return kUnitSubs;
     default: return -1;
   }
 }
@@ -766,17 +768,19 @@ void retire(Engine &E, Run &r) {
   const ce_insn &I = r.code[r.pc];
   E.complete(*r.cur);
   RegFile &R = E.regs(r.client);
-  if (I.op == kCmp) {
-    for (int k = 0; k < 4; ++k) {
-      E.unref(R.nzcv[k]);
-      R.nzcv[k] = r.cur->result[k];
-    }
-  } else {
+  // CMP: result = NZCV; ADDS/SUBS: rd bits then NZCV; others: rd bits
+  const bool flags = I.op == kCmp || I.op == kAdds || I.op == kSubs;
+  const int first_flag = I.op == kCmp ? 0 : kWidth;
+  if (I.op != kCmp)
     for (int j = 0; j < kWidth; ++j) {
       E.unref(R.r[I.rd][j]);
       R.r[I.rd][j] = r.cur->result[j];
     }
-  }
+  if (flags)
+    for (int k = 0; k < 4; ++k) {
+      E.unref(R.nzcv[k]);
+      R.nzcv[k] = r.cur->result[first_flag + k];
+    }
   r.cur.reset();
   ++r.pc;
 }

@@ -297,21 +297,29 @@ bool build_unit(int unit, int w, int cond, Netlist *out) {
       for (int k = 0; k < w; ++k) o.push_back(B.gate(AND, Q[k], nz));
       break;
     }
-    case kUnitCmp: {
-      std::vector<Ref> nb(w);
-      for (int i = 0; i < w; ++i) nb[i] = !b[i];
-      AdderOut r = kogge_stone(B, a, nb, 1, Ref{});
+    case kUnitCmp:
+    case kUnitSubs:
+    case kUnitAdds: {
+      const bool add = unit == kUnitAdds;
+      std::vector<Ref> bb(w);
+      for (int i = 0; i < w; ++i) bb[i] = add ? b[i] : !b[i];
+      AdderOut r = add ? kogge_stone(B, a, bb, 0, Ref{}) : kogge_stone(B, a, bb, 1, Ref{});
       const Ref s = r.sum[w - 1];
       const Ref N = s;
       const Ref Z = !or_tree(B, r.sum);
       const Ref C = r.carry;
-      // §6: V = (!a !b' s) + (a b' !s) applied to a, b' = NOT b, s.
-      const Ref x1 = B.gate(ANDNY, a[w - 1], b[w - 1]);
+      // §6: V = (!x !y s) + (x y !s) for the added operands x = a, y = b
+      // (ADDS) or y = NOT b (CMP, SUBS), in gates on a and b.
+      const Ref x1 = B.gate(add ? NOR : ANDNY, a[w - 1], b[w - 1]);
       const Ref x2 = B.gate(AND, x1, s);
-      const Ref y1 = B.gate(ANDYN, a[w - 1], b[w - 1]);
+      const Ref y1 = B.gate(add ? AND : ANDYN, a[w - 1], b[w - 1]);
       const Ref y2 = B.gate(ANDYN, y1, s);
       const Ref V = B.gate(OR, x2, y2);
-      o = {N, Z, C, V};
+      if (unit != kUnitCmp) o = r.sum;
+      o.push_back(N);
+      o.push_back(Z);
+      o.push_back(C);
+      o.push_back(V);
       break;
     }
     case kUnitCsel: {

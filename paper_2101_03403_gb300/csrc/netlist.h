@@ -59,11 +59,14 @@ enum Unit : int {
   kUnitAsr = 11,       // arithmetic right shift (§5 "Arithmetic right shift")
   kUnitEor = 12,       // bitwise XOR (§5 "Bitwise operations")
   kUnitOrn = 13,       // bitwise a OR NOT b
-  kUnitCount = 14
+  kUnitAdds = 14,      // a + b and its NZCV (flag-setting add, §6)
+  kUnitSubs = 15,      // a - b and its NZCV (CMP that keeps the difference)
+  kUnitCount = 16
 };
 
 // Inputs: a[width] then b[width] (CSEL: rn[width], rm[width], N, Z, C, V).
-// Outputs: width bits (CMP: N, Z, C, V).  Returns false for a bad request.
+// Outputs: width bits (CMP: N, Z, C, V; ADDS/SUBS: width bits then N, Z, C,
+// V).  Returns false for a bad request.
 bool build_unit(int unit, int width, int cond, Netlist *out);
 
 }  // namespace ce

@@ -56,17 +56,23 @@ def operands(rng, n):
 
 
 @pytest.mark.parametrize("unit", ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "CMP",
-                                  "LSR", "ASR", "EOR", "ORN"])
+                                  "LSR", "ASR", "EOR", "ORN", "ADDS", "SUBS"])
 def test_unit_semantics(ce, ctx, keys, unit):
     sk, _ = keys
-    rng = np.random.default_rng(hash(unit) % 1000)
+    rng = np.random.default_rng(sum(map(ord, unit)))
     n = 40
     a, b = operands(rng, n)
-    out = run_unit(ce, ctx, unit, enc_operands(ce, sk, operand_bits(a, b), 5), 4 if unit == "CMP" else W)
+    n_out = {"CMP": 4, "ADDS": W + 4, "SUBS": W + 4}.get(unit, W)
+    out = run_unit(ce, ctx, unit, enc_operands(ce, sk, operand_bits(a, b), 5), n_out)
     bits = decrypt_all(ce, sk, out)
     for i in range(n):
         exp = NL.armv8(unit, int(a[i]), int(b[i]), W)
-        got = list(bits[i]) if unit == "CMP" else NL.from_bits(bits[i])
+        if unit == "CMP":
+            got = list(bits[i])
+        elif unit in ("ADDS", "SUBS"):
+            got = [NL.from_bits(bits[i][:W])] + list(bits[i][W:])
+        else:
+            got = NL.from_bits(bits[i])
         assert got == exp, (unit, int(a[i]), int(b[i]), got, exp)
 
 

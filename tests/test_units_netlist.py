@@ -8,7 +8,7 @@ import pytest
 from oracle import netlists as NL
 
 UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "LSR", "ASR",
-         "EOR", "ORN"]
+         "EOR", "ORN", "ADDS", "SUBS"]
 
 
 def eval_vec(net, inputs):
@@ -40,6 +40,12 @@ def check_unit(unit, w, a, b, cond=0, nzcv=None):
         exp = np.array([NL.armv8(unit, int(x), int(y), w) for x, y in zip(a, b)])
         for k in range(4):
             assert (outs[k] == exp[:, k]).all(), (unit, k)
+    elif unit in ("ADDS", "SUBS"):
+        exp = np.array([NL.armv8(unit, int(x), int(y), w) for x, y in zip(a, b)])
+        got = sum(outs[i].astype(np.int64) << i for i in range(w))
+        assert (got == exp[:, 0]).all(), unit
+        for k in range(4):
+            assert (outs[w + k] == exp[:, 1 + k]).all(), (unit, k)
     else:
         got = sum(outs[i].astype(np.int64) << i for i in range(w))
         if unit == "CSEL":
@@ -103,6 +109,24 @@ def test_right_shifts_are_the_reversed_left_shift():
     fill = np.where(sign == 1, (0xFF << (8 - s)) & 0xFF, 0)
     assert (val(asr) == (val(lsr) | fill)).all()
     assert (val(lsl) == (a << s) & 0xFF).all()
+
+
+def test_flag_setting_flags_by_brute_force():
+    """ADDS/SUBS flags at width 8 from their definitions on signed and
+    unsigned integers (independent of the ARMv8 model)."""
+    a, b = np.meshgrid(np.arange(256), np.arange(256))
+    a, b = a.ravel(), b.ravel()
+    sgn = lambda x: np.where(x >= 128, x - 256, x)
+    ins = [(a >> i) & 1 for i in range(8)] + [(b >> i) & 1 for i in range(8)]
+    for unit, r_u, r_s, carry in (("ADDS", a + b, sgn(a) + sgn(b), a + b > 255),
+                                  ("SUBS", a - b, sgn(a) - sgn(b), a >= b)):
+        outs = eval_vec(NL.build(unit, 8), ins)
+        r = r_u & 255
+        assert (sum(outs[i].astype(np.int64) << i for i in range(8)) == r).all()
+        assert (outs[8] == (r >> 7)).all()                       # N
+        assert (outs[9] == (r == 0)).all()                       # Z
+        assert (outs[10] == carry).all()                         # C
+        assert (outs[11] == ((r_s < -128) | (r_s > 127))).all()  # V
 
 
 def test_right_shift_structure():

@@ -7,8 +7,8 @@ key's negacyclic Toeplitz blocks, key words in four balanced byte limbs and
 digits in two balanced 5-bit limbs (fp16 operands, exact fp32 sums).
 Ciphertexts must equal the oracle word for word (all of them for small
 batches, sampled ones for large), and the transform form on every output:
-across gate tiles of 128 with ragged tails, K splits of 8, 4, 3 and 1 (the
-launcher's choice for 1, 2, 3 and 10 tiles; 19 tiles run unsplit), zero
+across gate tiles of 128 with ragged tails, K splits of 8, 4 and 3 (the
+launcher's choice for 1, 2, and 3 or 10 tiles) and unsplit (19 tiles), zero
 rotations, MUX pairs, and the levels of a 16-bit unit run by the netlist
 engine.
 """

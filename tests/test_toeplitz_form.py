@@ -91,7 +91,9 @@ def test_core_matrix_walk_reproduces_operand_tiles():
     Q = 2 * N // 8 - 1
     q, r, c = np.meshgrid(np.arange(Q), np.arange(8), np.arange(8), indexing="ij")
     cm = fl[8 * q + r + c].reshape(-1)                   # halves, 64 per core matrix
-    for n0, k0, s in ((0, 0, 0), (896, 960, 3), (384, 128, 1)):
+    # (n0, k0, s): tile origin and K-step; (896, 768, 15) is the last K-step of
+    # the last 256-wide chunk of the last coefficient tile: core matrix 254
+    for n0, k0, s in ((0, 0, 0), (896, 960, 3), (384, 128, 1), (896, 768, 15)):
         start = (n0 + k0) // 8 * 128 + s * 256            # bytes
         nn = np.arange(128)[:, None]
         kk = np.arange(16)[None, :]

@@ -15,9 +15,12 @@ seed 20210103).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 `value` uses device-resident inputs (device-side time of K steps, L2 flushed
-between steps); `e2e` runs the same steps through the same public call
-(ce_unit_eval_device) with the copy of the step's inputs from pinned host
-memory and of its results back to the host inside the timed region.
+between steps); `e2e` runs the same steps through the library's host-buffer
+call (ce_unit_eval: the step's inputs copied from pinned host memory and its
+results copied back inside the call, inside the timed region).  Latency:
+one 16-bit ADD and one 16-bit MUL alone (graph replay, CUDA events, 20+
+repeats), and a short serving run (16 clients with their own keys,
+ADD/SUB/MUL/UDIV 40/30/20/10 at Poisson arrivals) for per-request p50/p99.
 `--impl reference` times the plain CPU oracle (test infrastructure, used here
 only as the reference arm) on a bounded sample of the same workload.
 Under torchrun every rank evaluates its own batch (independent gates, no
@@ -53,11 +56,17 @@ UNIT = "gates/s"
 BFLY_PER_CMUX = 2 * 8 * 512 * 10                               # 81,920
 MAC_PER_CMUX = 2 * 12 * 1024                                   # 24,576
 OPS_PER_GATE = 500 * (7 * BFLY_PER_CMUX + 2.5 * MAC_PER_CMUX)   # 317,440,000
-# Integer issue peak from unit counts: 152 SMs x 4 schedulers x 32 lanes x
-# 2.07 GHz (multiply-adds and other integer operations issue to separate
-# 64-lane pipes; a probe measures 124 int32 operations per clock per SM for
-# an even mix).
-PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12                          # 40.27
+# Integer issue peak from unit counts: SMs x 4 schedulers x 32 lanes x SM
+# clock (multiply-adds and other integer operations issue to separate 64-lane
+# pipes).  The SM count is read from the device and the clock is the median
+# sampled during the timed region.
+INT_LANES_PER_SM = 128
+
+
+def int_peak_tops(sms: int, sm_mhz: float) -> float:
+    return sms * INT_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+
+
 KERNEL_SOURCES = ["bootstrap_kernels.cu", "rns_ntt.cuh", "rns_arith.h"]
 N_PAIRS = 256
 # External-product forms compared on one gate batch (19 tiles of 128 gates:
@@ -318,17 +327,14 @@ def run_ours(args, rank: int, world: int, local: int):
     torch.cuda.synchronize(dev)
     graph_value = boots * args.steps / (g0.elapsed_time(g1) / 1e3)
 
-    # end to end: pinned host inputs -> device -> unit -> host, per step
+    # end to end through the host-buffer call: pinned host inputs -> device ->
+    # unit (captured graph) -> pinned host results, all inside ce_unit_eval
     pin_in = torch.from_numpy(host_in.view(np.int32)).pin_memory()
     pin_out = torch.empty((n, 16, 501), dtype=torch.int32).pin_memory()
-    e2e_in = torch.empty_like(d_in)
-    e2e_out = torch.empty_like(d_out)
+    h_in, h_out = pin_in.numpy().view(np.uint32), pin_out.numpy().view(np.uint32)
 
     def e2e_step():
-        e2e_in.copy_(pin_in, non_blocking=True)
-        ce.ce_unit_eval_device(ctx, cid, "ADD", e2e_in, e2e_out, n, 0, stream)
-        pin_out.copy_(e2e_out, non_blocking=True)
-        stream.synchronize()
+        ce.ce_unit_eval(ctx, cid, "ADD", h_in, h_out)
 
     e2e_step()
     barrier(world)
@@ -337,7 +343,29 @@ def run_ours(args, rank: int, world: int, local: int):
         e2e_step()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     e2e_val = boots * args.steps * world / e2e_s
-    assert (pin_out.numpy() == d_out.cpu().numpy()).all(), "e2e output differs"
+    assert (h_out == d_out.cpu().numpy().view(np.uint32)).all(), "e2e output differs"
+
+    # latency of one instruction alone: one operand pair, graph replay
+    def alone_ms(unit, reps):
+        x = rng.integers(0, 1 << 16, 2)
+        d1 = torch.from_numpy(encrypt_operands(ce, sk, x[:1], x[1:], 91).view(np.int32)).to(dev)
+        o1 = torch.empty((1, 16, 501), dtype=torch.int32, device=dev)
+        ce.ce_unit_eval_device(ctx, cid, unit, d1, o1, 1, 0, stream)    # plan + capture
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ce.ce_unit_eval_device(ctx, cid, unit, d1, o1, 1, 0, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        want = {"ADD": (int(x[0]) + int(x[1])) & 0xFFFF, "MUL": (int(x[0]) * int(x[1])) & 0xFFFF}
+        assert decrypt_word(ce, sk, o1.cpu().numpy().view(np.uint32)[0]) == want[unit]
+        return ts
+
+    add1_ms = alone_ms("ADD", 30)
+    mul1_ms = alone_ms("MUL", 20)
 
     # 16-bit MUL latency on 64 pairs (array multiplier)
     mul_n = 64
@@ -359,15 +387,21 @@ def run_ours(args, rank: int, world: int, local: int):
         assert decrypt_word(ce, sk, mo[i]) == (int(ma[i]) * int(mb[i])) & 0xFFFF, "wrong product"
     mul_boots = mul_n * ce.ce_unit_info("MUL")["n_bootstraps"]
 
-    forms = external_product_forms(ce, ctx, cid, stream, dev, rng, d_min, d_mout, mul_n) \
-        if rank == 0 else None
+    clocks = clk.summary()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    peak_tops = int_peak_tops(sms, sm_mhz)
+    forms = external_product_forms(ce, ctx, cid, stream, dev, rng, d_min, d_mout, mul_n,
+                                   peak_tops) if rank == 0 else None
+    serving = serving_leg(ce, ctx) if rank == 0 else None
 
     br_ms, br_launches = prof["blind_rotate"]
     achieved = boots * args.steps * OPS_PER_GATE / (br_ms / 1e3) / 1e12
     roof = {"kernel": "blind_rotate", "bound": "alu", "achieved": achieved,
-            "peak": PEAK_TOPS, "unit": "Tops/s (int32)", "frac": achieved / PEAK_TOPS,
+            "peak": peak_tops, "unit": "Tops/s (int32)", "frac": achieved / peak_tops,
             "traffic": recorded_traffic("blind_rotate", args.steps and br_launches / args.steps),
-            "peak_note": "derived: 152 SMs x 128 int32 lanes per clock x 2.07 GHz; "
+            "peak_note": f"derived: {sms} SMs x {INT_LANES_PER_SM} int32 lanes per clock x "
+                         f"{sm_mhz:.0f} MHz (median SM clock sampled in the timed region); "
                          "work = 7 ops per transform butterfly + 2.5 per multiply-accumulate",
             "launches_per_step": br_launches / args.steps,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
@@ -396,21 +430,43 @@ def run_ours(args, rank: int, world: int, local: int):
                            "parallelism": f"independent batches x{world}",
                            "graph_replay_gates_per_s": graph_value,
                            "autotuned_gates_per_block": tuned},
-                "latency_ms": {"add16_batch256_p50": pct(step_ms, 50),
-                               "add16_batch256_p99": pct(step_ms, 99),
+                "latency_ms": {"add16_alone_p50": pct(add1_ms, 50),
+                               "add16_alone_p99": pct(add1_ms, 99),
+                               "add16_alone_repeats": len(add1_ms),
+                               "mul16_alone_p50": pct(mul1_ms, 50),
+                               "mul16_alone_p99": pct(mul1_ms, 99),
+                               "mul16_alone_repeats": len(mul1_ms),
+                               "add16_batch256_step_p50": pct(step_ms, 50),
                                "mul16_batch64_p50": pct(mul_ms, 50),
-                               "mul16_batch64_p99": pct(mul_ms, 99),
                                "mul16_bootstraps": mul_boots},
+                "serving": serving,
                 "e2e": {"value": e2e_val, "unit": UNIT,
                         "h2d_bytes_per_step": int(host_in.nbytes),
                         "d2h_bytes_per_step": int(n * 16 * 501 * 4)},
-                "gpu_launches": launches, "roofline": roof, "clocks": clk.summary(),
+                "gpu_launches": launches, "roofline": roof, "clocks": clocks,
                 "cpu_baseline": cpu, "external_product_forms": forms}
         print(json.dumps(line), flush=True)
     ctx.close()
 
 
-def external_product_forms(ce, ctx, cid, stream, dev, rng, d_min, d_mout, mul_n):
+def serving_leg(ce, ctx, clients: int = 16, requests: int = 256, load: float = 0.9):
+    """Short serving run (the configs' request mix at Poisson arrivals, a
+    fraction of the measured saturated rate): per-request p50/p99 latency and
+    bootstraps/s.  Clients get their own seeded key sets."""
+    from paper_2101_03403_gb300 import serve_bench
+    res = serve_bench.serve(ce, ctx, clients, requests, [load], seed=SEED + 1000)
+    pt = res["points"][0]
+    return {"clients": res["clients_admitted"], "requests": pt["requests"], "load": load,
+            "mix": res["mix"], "requests_per_s": pt["requests_per_s"],
+            "bootstraps_per_s": pt["bootstraps_per_s"],
+            "latency_ms_p50": pt["latency_ms_p50"], "latency_ms_p99": pt["latency_ms_p99"],
+            "latency_ms_p50_by_op": pt["latency_ms_p50_by_op"],
+            "latency_ms_p99_by_op": pt["latency_ms_p99_by_op"],
+            "saturated_requests_per_s": res["saturated"]["requests_per_s"],
+            "saturated_bootstraps_per_s": res["saturated"]["bootstraps_per_s"]}
+
+
+def external_product_forms(ce, ctx, cid, stream, dev, rng, d_min, d_mout, mul_n, peak_tops):
     """The blind rotation's external products in both forms on one batch of
     XP_GATES seeded gates and on the MUL-64 unit: the two-prime transform on
     the CUDA cores (default) and the Toeplitz contraction on the tensor cores.
@@ -470,8 +526,8 @@ def external_product_forms(ce, ctx, cid, stream, dev, rng, d_min, d_mout, mul_n)
             ms = prof["blind_rotate"][0]
             ach = n * OPS_PER_GATE / (ms / 1e3) / 1e12
             entry["roofline"] = {"kernel": "blind_rotate", "bound": "alu", "achieved": ach,
-                                 "peak": PEAK_TOPS, "unit": "Tops/s (int32)",
-                                 "frac": ach / PEAK_TOPS}
+                                 "peak": peak_tops, "unit": "Tops/s (int32)",
+                                 "frac": ach / peak_tops}
         else:
             ms, cnt = prof["external_product_mma"]
             ach = n * XP_FLOPS_PER_GATE / (ms / 1e3) / 1e12

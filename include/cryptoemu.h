@@ -28,7 +28,11 @@
  *    the given stream has finished; those calls are asynchronous.
  *  - Everything the context allocates on the device (keys, scratch) is owned
  *    by the context and released by ce_destroy / ce_client_evict.
- *  - A context is not thread-safe: one host thread at a time per context.
+ *  - Calls on one context may come from several host threads (a serving
+ *    loop's worker is one): the calls that enqueue GPU work take the
+ *    context's lock, and each one's GPU work is ordered after the previous
+ *    one's, whichever stream either used.  ce_destroy must not race with any
+ *    other call on the context, and needs every serving loop destroyed first.
  */
 #ifndef CRYPTOEMU_H
 #define CRYPTOEMU_H
@@ -46,6 +50,8 @@ extern "C" {
 #define CE_BSK_WORDS (500u * 6u * 2u * 1024u)        /* 3,072,000 uint32 */
 #define CE_KSK_WORDS (1024u * 8u * 4u * 501u)        /* 16,416,768 uint32 */
 
+/* Status of every call (the paper's emulator has no error model; these are
+ * this library's). */
 typedef enum {
     CE_OK = 0,
     CE_EINVAL = -1,     /* bad argument (null pointer, size, opcode, id) */
@@ -63,9 +69,12 @@ typedef enum {
     CE_ANDNY = 6, CE_ANDYN = 7, CE_ORNY = 8, CE_ORYN = 9
 } ce_gate_op;
 
-/* One LWE ciphertext: 2004 bytes, a[0..499] then b. */
+/* One LWE ciphertext (§3 "TFHE Library": the encrypted bit every gate takes
+ * and returns): 2004 bytes, a[0..499] then b. */
 typedef struct { uint32_t a[CE_LWE_N]; uint32_t b; } ce_lwe;
 
+/* The cloud side of §4 "Cloud service model": holds the admitted clients'
+ * cloud keys on the GPU, their encrypted register files and scratch. */
 typedef struct ce_ctx ce_ctx;
 
 /* ------------------------------------------------------------- client --- */
@@ -74,7 +83,8 @@ typedef struct ce_ctx ce_ctx;
  * s[500] and the TRLWE key K[1024] as uint32 values in {0,1}.  Each bit is the
  * top bit of one uniform draw of the counter-based SplitMix64 stream
  * described in ce_cloud_keygen.  The buffer is allocated by the library and
- * freed with ce_free. */
+ * freed with ce_free.  (§4 "Cloud service model": the user owns the secret
+ * key; §3: the TFHE library's key generation.) */
 #define CE_SECRET_BYTES (8u + 4u * (500u + 1024u))
 ce_status ce_secret_keygen(uint64_t seed, void **secret_out, size_t *bytes_out);
 
@@ -106,23 +116,39 @@ int ce_decrypt_bit(const void *secret, const ce_lwe *c);
 
 /* ------------------------------------------------------------- context --- */
 
-/* Create a context on CUDA device `device`.  `hbm_budget_bytes` caps the
- * device memory the context's clients may hold (0 = 90% of the free memory
- * at creation).  `cuda_stream` (a cudaStream_t, may be NULL for the legacy
- * default stream) is the stream all synchronous calls enqueue on. */
+/* Create a context on CUDA device `device` (§4 "Cloud service model": the
+ * cloud that evaluates instructions over its users' encrypted data).
+ * `hbm_budget_bytes` caps the device memory the context's clients may hold
+ * (0 = 90% of the free memory at creation).  `cuda_stream` (a cudaStream_t,
+ * may be NULL for the legacy default stream) is the stream all synchronous
+ * calls enqueue on.  CE_ECUDA without a device, CE_EINVAL for a bad index. */
 ce_status ce_create(ce_ctx **out, int device, uint64_t hbm_budget_bytes,
                     void *cuda_stream);
+/* Waits for all work on the device, then frees everything the context owns
+ * (keys, registers, scratch).  NULL is ignored. */
 void ce_destroy(ce_ctx *ctx);
+/* Message of the calling thread's last failed call (this library's error
+ * model; the paper has none).  Valid until that thread's next failing call. */
 const char *ce_last_error(void);
+/* Device allocations (cudaMalloc) and frees the library has made in this
+ * process, for callers that budget device memory and for tests (the paper
+ * has no counterpart).  Either pointer may be NULL. */
+void ce_device_alloc_count(uint64_t *allocations, uint64_t *frees);
 
-/* Admit a client: copies its cloud key (CE_CLOUD_BYTES host bytes) to the
+/* Admit a client (§4 "Cloud service model": a user hands the cloud the
+ * public material its homomorphic evaluation needs): copies its cloud key
+ * (CE_CLOUD_BYTES host bytes, caller-owned, read during the call) to the
  * device and converts the bootstrapping key to the negacyclic-transform
  * domain used by the blind-rotation kernel (98,304 B per key bit); the
  * coefficient key stays resident too (for the tensor-core external product).
  * Returns CE_EADMIT when the client's device footprint would exceed the
- * budget. */
+ * budget, CE_EINVAL for bytes that are not a cloud key. */
 ce_status ce_client_admit(ce_ctx *ctx, const void *cloud_key, size_t bytes,
                           int *client_id);
+/* Evict a client (§4: the user leaves the cloud): waits for all work on the
+ * device, then frees its keys, registers and cached unit plans.
+ * CE_ENOTFOUND for an unknown id; CE_EINVAL while a serving loop has one of
+ * its requests queued or running (wait for them first). */
 ce_status ce_client_evict(ce_ctx *ctx, int client_id);
 /* Device bytes a client holds at admission (keys + register file; the
  * tensor-core external product adds its key form on first use). */
@@ -130,12 +156,17 @@ uint64_t ce_client_footprint_bytes(void);
 
 /* ---------------------------------------------------------------- gates --- */
 
-/* One bootstrapped gate out = op(a, b) with host ciphertexts (blocking). */
+/* One bootstrapped gate out = op(a, b) with host ciphertexts (blocking):
+ * one of the bootstrapped gates of §3, Table "TFHE API Benchmark".
+ * CE_EINVAL for a bad opcode or NULL buffer, CE_ENOTFOUND for an unknown
+ * client. */
 ce_status ce_gate(ce_ctx *ctx, int client, ce_gate_op op, const ce_lwe *a,
                   const ce_lwe *b, ce_lwe *out);
-/* n independent gates out[i] = ops[i](a[i], b[i]) with host buffers: copies
- * the inputs to the device, runs the batched path and copies the results
- * back (blocking).  ops: n bytes (ce_gate_op values). */
+/* n independent gates out[i] = ops[i](a[i], b[i]) with host buffers (§3,
+ * Table "TFHE API Benchmark", batched as the independent gates of §5's
+ * OpenMP sections): copies the inputs to the device, runs the batched path
+ * and copies the results back (blocking).  ops: n bytes (ce_gate_op
+ * values). */
 ce_status ce_gates_batch(ce_ctx *ctx, int client, const uint8_t *ops,
                          const ce_lwe *a, const ce_lwe *b, ce_lwe *out, size_t n);
 /* Same on device buffers (d_ops: n bytes; d_a, d_b, d_out: n x 501 uint32,
@@ -273,6 +304,14 @@ ce_status ce_unit_eval_device(ce_ctx *ctx, int client, int unit, int cond,
 ce_status ce_unit_eval_device_width(ce_ctx *ctx, int client, int unit, int cond, int width,
                                     const uint32_t *d_in, uint32_t *d_out, size_t n,
                                     void *cuda_stream);
+/* The same with host buffers (blocking): in is [n][n_inputs] host
+ * ciphertexts, out [n][n_outputs]; the call copies the inputs to
+ * context-owned device buffers, replays the unit's plan (captured graph) on
+ * the context's stream and copies the results back.  Use pinned host memory
+ * for full copy bandwidth.  Errors as ce_unit_eval_device, plus CE_ETIMEOUT /
+ * CE_EINVAL for a device-side failure of this call's work. */
+ce_status ce_unit_eval(ce_ctx *ctx, int client, int unit, int cond, int width,
+                       const ce_lwe *in, ce_lwe *out, size_t n);
 /* Graph replay of ce_unit_eval_device on (1, default) or off (eager). */
 ce_status ce_set_unit_graphs(ce_ctx *ctx, int on);
 
@@ -283,24 +322,27 @@ ce_status ce_set_unit_graphs(ce_ctx *ctx, int on);
  * machine over vRegs; §6 conditional flags).  The program counter and the
  * instructions are cleartext; registers and flags stay encrypted. */
 typedef enum {
-    CE_I_ADD = 0,      /* rd = rn + rm (parallel-prefix adder) */
-    CE_I_SUB = 1,      /* rd = rn - rm */
-    CE_I_AND = 2,      /* rd = rn & rm */
-    CE_I_ORR = 3,      /* rd = rn | rm */
-    CE_I_LSL = 4,      /* rd = rn << (rm mod 16) (barrel shifter) */
-    CE_I_LSL_IMM = 5,  /* rd = rn << (imm mod 16) (no bootstrap) */
-    CE_I_MUL = 6,      /* rd = (rn * rm) mod 2^16 */
-    CE_I_UDIV = 7,     /* rd = rn / rm, 0 when rm = 0 */
-    CE_I_CMP = 8,      /* NZCV = flags(rn - rm) */
-    CE_I_CSEL = 9,     /* rd = cond(NZCV) ? rn : rm (cond as for CE_U_CSEL) */
-    CE_I_MOV = 10,     /* rd = rn (no bootstrap) */
-    CE_I_MOV_IMM = 11, /* rd = imm (8-bit, zero extended; trivial ciphertexts) */
-    CE_I_LSR = 12,     /* rd = rn >> (rm mod 16), logical (barrel shifter) */
-    CE_I_ASR = 13,     /* rd = rn >> (rm mod 16), arithmetic */
+    CE_I_ADD = 0,      /* rd = rn + rm (§5 "Adder": parallel-prefix adder) */
+    CE_I_SUB = 1,      /* rd = rn - rm (§5 "Subtractor") */
+    CE_I_AND = 2,      /* rd = rn & rm (§5 "Bitwise operations") */
+    CE_I_ORR = 3,      /* rd = rn | rm (§5 "Bitwise operations") */
+    CE_I_LSL = 4,      /* rd = rn << (rm mod 16) (§5 "Shifter": barrel shifter) */
+    CE_I_LSL_IMM = 5,  /* rd = rn << (imm mod 16) (§5 "Shifter", shift immediate: no bootstrap) */
+    CE_I_MUL = 6,      /* rd = (rn * rm) mod 2^16 (§5 "Multiplier") */
+    CE_I_UDIV = 7,     /* rd = rn / rm, 0 when rm = 0 (§5 "Divider") */
+    CE_I_CMP = 8,      /* NZCV = flags(rn - rm) (§6 "Conditional Flags") */
+    CE_I_CSEL = 9,     /* rd = cond(NZCV) ? rn : rm (cond as for CE_U_CSEL; §6
+                          conditional execution on the encrypted flags) */
+    CE_I_MOV = 10,     /* rd = rn (§5 "Data movement": COPY, no bootstrap) */
+    CE_I_MOV_IMM = 11, /* rd = imm (8-bit, zero extended; trivial ciphertexts:
+                          §3 CONSTANT) */
+    CE_I_LSR = 12,     /* rd = rn >> (rm mod 16), logical (§5 "Logic right
+                          shift/Arithmetic right shift": barrel shifter) */
+    CE_I_ASR = 13,     /* rd = rn >> (rm mod 16), arithmetic (same passage) */
     CE_I_LSR_IMM = 14, /* rd = rn >> (imm mod 16), logical (no bootstrap) */
     CE_I_ASR_IMM = 15, /* rd = rn >> (imm mod 16), arithmetic (no bootstrap) */
-    CE_I_EOR = 16,     /* rd = rn ^ rm */
-    CE_I_ORN = 17,     /* rd = rn | ~rm */
+    CE_I_EOR = 16,     /* rd = rn ^ rm (§5 "Bitwise operations") */
+    CE_I_ORN = 17,     /* rd = rn | ~rm (§5 "Bitwise operations") */
     /* §5 "Bitwise operations" with an immediate and NOT, and "Data movement":
      * no bootstrap (wire copies, negations and constants).  imm: 8 bits, zero
      * extended; BFC/BFI: field lsb = imm & 15, width = (imm >> 4) + 1, clipped
@@ -313,30 +355,42 @@ typedef enum {
     CE_I_BFI = 23,     /* rd[lsb, lsb + width) = rn[0, width) */
     CE_I_RBIT = 24,    /* rd = rn with the bit order reversed */
     CE_I_REV = 25,     /* rd = rn with the two bytes swapped */
-    CE_I_ADDS = 26,    /* rd = rn + rm, NZCV = its flags (§6 flag-setting form) */
-    CE_I_SUBS = 27     /* rd = rn - rm, NZCV = flags(rn - rm) */
+    CE_I_ADDS = 26,    /* rd = rn + rm, NZCV = its flags (§6 "Conditional Flags":
+                          the flag-setting form) */
+    CE_I_SUBS = 27     /* rd = rn - rm, NZCV = flags(rn - rm) (§6, the SUBS example) */
 } ce_opcode;
+/* One cleartext instruction (§4 "Cloud service model": HE instructions are
+ * unencrypted; §4 "Data Processing": register operands rd, rn, rm are vReg
+ * indices 0..7, imm an 8-bit immediate, cond a condition code as for
+ * CE_U_CSEL). */
 typedef struct { uint8_t op, rd, rn, rm, imm, cond; } ce_insn;
 
-/* Register file access with host ciphertexts (bit 0 first; blocking).
- * Registers not written hold trivial encryptions of 0. */
+/* Register file access with host ciphertexts (bit 0 first; blocking): the
+ * encrypted vRegs of §4 "Data Processing", which the user fills and reads
+ * through the cloud service model (§4 "Cloud service model").  Registers
+ * not written hold trivial encryptions of 0.  CE_EINVAL for reg outside
+ * 0..7, CE_ENOTFOUND for an unknown client. */
 ce_status ce_reg_write(ce_ctx *ctx, int client, int reg, const ce_lwe bits[16]);
 ce_status ce_reg_read(ce_ctx *ctx, int client, int reg, ce_lwe bits[16]);
+/* The encrypted NZCV flags (§6 "Conditional Flags"), N first. */
 ce_status ce_flags_read(ce_ctx *ctx, int client, ce_lwe nzcv[4]);
-/* Runs a program to completion on the client's registers (blocking on the
- * host until every instruction is enqueued; results are read with
- * ce_reg_read).  Malformed instructions give CE_EINVAL; timeout_ns > 0
- * bounds the host time (CE_ETIMEOUT). */
+/* Runs a program to completion on the client's registers (§4: the emulator
+ * fetches cleartext instructions and runs them over encrypted vRegs; §6
+ * "Branch and Control Flow" for the flags): blocking on the host until every
+ * instruction is enqueued; results are read with ce_reg_read.  Malformed
+ * instructions give CE_EINVAL; timeout_ns > 0 bounds the host time
+ * (CE_ETIMEOUT). */
 ce_status ce_exec(ce_ctx *ctx, int client, const ce_insn *prog, size_t n, uint64_t timeout_ns);
-/* Runs several programs concurrently: their instructions advance level by
- * level together, so gates of different programs and clients share each
- * batched launch. */
+/* Runs several programs concurrently (§5: independent work of the emulator
+ * runs in parallel; here across programs and clients): their instructions
+ * advance level by level together, so gates of different programs and
+ * clients share each batched launch. */
 ce_status ce_exec_multi(ce_ctx *ctx, size_t n_programs, const int *clients,
                         const ce_insn *const *progs, const size_t *lens, uint64_t timeout_ns);
 
 /* ---------------------------------------------------------------- serving --- */
 
-/* A serving loop on a context (§4 cloud service model): requests are single
+/* A serving loop on a context (§4 "Cloud service model"): requests are single
  * instructions (ce_insn) on a client's encrypted registers, submitted from
  * any host thread.  A worker thread batches them continuously: each tick
  * starts queued requests (one in flight per client, so each client's
@@ -344,11 +398,14 @@ ce_status ce_exec_multi(ce_ctx *ctx, size_t n_programs, const int *clients,
  * limit), runs one level of every in-flight instruction of every client in
  * one batched launch, and retires finished ones.  Requests arriving while
  * others run join at the next tick.  Results are bit-identical to running
- * the same instruction alone.  While a server runs, other calls on the same
- * context are serialised with it. */
+ * the same instruction alone.  While a server runs, the context's other
+ * calls take turns with its ticks (the context lock) and their GPU work is
+ * ordered with the ticks' work. */
 typedef struct ce_server ce_server;
 ce_status ce_server_create(ce_ctx *ctx, int max_inflight, ce_server **out);
-/* Enqueue one instruction for `client`; *ticket identifies the request. */
+/* Enqueue one instruction (any ce_opcode) for `client`; *ticket identifies
+ * the request.  CE_ENOTFOUND for an unknown client, CE_EINVAL for a
+ * malformed instruction. */
 ce_status ce_server_submit(ce_server *s, int client, const ce_insn *insn, uint64_t *ticket);
 /* Non-blocking status; times are steady-clock nanoseconds (submission,
  * start on the GPU path, completion of its GPU work). */
@@ -376,10 +433,47 @@ void ce_server_destroy(ce_server *s);
  * scratch word needs to start at zero: each call writes everything it reads.
  * The keys are the client's keys held by the context (admitted earlier).
  * It always uses the transform form of the external products and the
- * CUDA-core key switch (whose scratch fits the fixed area). */
+ * CUDA-core key switch (whose scratch fits the fixed area).  Its launches
+ * appear in ce_profile_read and ce_last_launch_count like the others. */
 ce_status ce_gates_batch_device_noalloc(ce_ctx *ctx, int client, const uint8_t *d_ops,
                                         const uint32_t *d_a, const uint32_t *d_b,
                                         uint32_t *d_out, size_t n, void *cuda_stream);
+
+/* ------------------------------------------------------------ gate trace --- */
+
+/* One traced gate of the netlist engine (for verification; the paper has no
+ * counterpart): the gate exactly as the GPU evaluated it, so that a plain
+ * CPU implementation can recompute its output from the GPU's own inputs.
+ * op: 0..9 a ce_gate_op on (in[0], in[1]); 10 MUX in[0] ? in[1] : in[2].
+ * neg[i]: input i enters negated (the netlist's free NOT).  in[i] are the
+ * words stored on the GPU before that negation (in[2] is zero unless MUX).
+ * tick: the engine tick (one level of every in-flight instruction) counted
+ * from ce_trace_enable; index: the gate's output position within its tick. */
+typedef struct {
+    int32_t op;
+    int32_t neg[3];
+    int32_t client;
+    uint32_t tick;
+    uint32_t index;
+    uint32_t pad;
+    ce_lwe in[3];
+    ce_lwe out;
+} ce_trace_rec;
+/* Start (per_tick > 0) or stop (0) tracing: from now on every engine tick
+ * (functional units, programs, serving) records up to per_tick of its gates,
+ * spread evenly over the tick's outputs, into a context-owned device buffer
+ * of cap records (each 8,048 bytes; records beyond cap are counted but not
+ * kept).  Waits for all work on the device and clears earlier records.
+ * While tracing, units run eagerly instead of as captured graphs (same
+ * kernels, same results) plus one small copy kernel per tick.  CE_EINVAL for
+ * per_tick above 4096 or cap outside 1..2^20 (when per_tick > 0). */
+ce_status ce_trace_enable(ce_ctx *ctx, int per_tick, size_t cap);
+/* Copies up to cap of the records kept since the last read into out (host
+ * memory), in the order the GPU wrote them, and clears them: *count = records
+ * copied, *seen (may be NULL) = records made, kept or not.  Waits for all
+ * work on the device. */
+ce_status ce_trace_read(ce_ctx *ctx, ce_trace_rec *out, size_t cap, size_t *count,
+                        uint64_t *seen);
 
 /* Per-kernel timing for measurement: while enabled, every kernel launch of
  * the gate path is bracketed by CUDA events on its own stream.

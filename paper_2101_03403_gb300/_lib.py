@@ -56,6 +56,7 @@ def lib() -> ctypes.CDLL:
         "ce_create": (i32, [pp, i32, u64, vp]),
         "ce_destroy": (None, [vp]),
         "ce_last_error": (ctypes.c_char_p, []),
+        "ce_device_alloc_count": (None, [ctypes.POINTER(u64), ctypes.POINTER(u64)]),
         "ce_client_admit": (i32, [vp, vp, sz, ctypes.POINTER(i32)]),
         "ce_client_evict": (i32, [vp, i32]),
         "ce_client_footprint_bytes": (u64, []),
@@ -77,6 +78,7 @@ def lib() -> ctypes.CDLL:
         "ce_unit_netlist": (i32, [i32, i32, i32, vp, sz, ctypes.POINTER(sz)]),
         "ce_unit_eval_device": (i32, [vp, i32, i32, i32, vp, vp, sz, vp]),
         "ce_unit_eval_device_width": (i32, [vp, i32, i32, i32, i32, vp, vp, sz, vp]),
+        "ce_unit_eval": (i32, [vp, i32, i32, i32, i32, vp, vp, sz]),
         "ce_set_unit_graphs": (i32, [vp, i32]),
         "ce_reg_write": (i32, [vp, i32, i32, vp]),
         "ce_reg_read": (i32, [vp, i32, i32, vp]),
@@ -93,6 +95,8 @@ def lib() -> ctypes.CDLL:
         "ce_server_destroy": (None, [vp]),
         "ce_autotune": (i32, [vp, i32, vp, vp, i32, ctypes.POINTER(i32)]),
         "ce_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), i32]),
+        "ce_trace_enable": (i32, [vp, i32, sz]),
+        "ce_trace_read": (i32, [vp, vp, sz, ctypes.POINTER(sz), ctypes.POINTER(u64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -320,12 +324,40 @@ def ce_selftest_device_wait(ctx: Context, limit_ns: int):
     _check(lib().ce_selftest_device_wait(ctx.ptr, limit_ns), "ce_selftest_device_wait")
 
 
+def ce_device_alloc_count() -> tuple[int, int]:
+    """(device allocations, device frees) the library has made in this process."""
+    a, f = ctypes.c_uint64(), ctypes.c_uint64()
+    lib().ce_device_alloc_count(ctypes.byref(a), ctypes.byref(f))
+    return a.value, f.value
+
+
 def ce_last_launch_count(ctx: Context) -> int:
     return int(lib().ce_last_launch_count(ctx.ptr))
 
 
 def ce_synchronize(ctx: Context):
     _check(lib().ce_synchronize(ctx.ptr), "ce_synchronize")
+
+
+# ce_trace_rec: op, neg[3], client, tick, index, pad, in[3][501], out[501]
+TRACE_DTYPE = np.dtype([("op", "<i4"), ("neg", "<i4", 3), ("client", "<i4"), ("tick", "<u4"),
+                        ("index", "<u4"), ("pad", "<u4"), ("inp", "<u4", (3, LWE_WORDS)),
+                        ("out", "<u4", LWE_WORDS)])
+assert TRACE_DTYPE.itemsize == 8048
+
+
+def ce_trace_enable(ctx: Context, per_tick: int, cap: int = 4096):
+    """Record up to per_tick gates of every engine tick (0 stops tracing)."""
+    _check(lib().ce_trace_enable(ctx.ptr, per_tick, cap), "ce_trace_enable")
+
+
+def ce_trace_read(ctx: Context, cap: int = 4096):
+    """(records as a TRACE_DTYPE array, records made since the last read)."""
+    out = np.zeros(cap, TRACE_DTYPE)
+    n, seen = ctypes.c_size_t(), ctypes.c_uint64()
+    _check(lib().ce_trace_read(ctx.ptr, out.ctypes.data, cap, ctypes.byref(n), ctypes.byref(seen)),
+           "ce_trace_read")
+    return out[:n.value], int(seen.value)
 
 
 KERNEL_KINDS = ["lincomb_modswitch", "blind_rotate", "extract_keyswitch", "external_product_mma"]
@@ -411,6 +443,19 @@ def ce_unit_eval_device_width(ctx: Context, client: int, unit, width: int, d_in,
     _check(lib().ce_unit_eval_device_width(ctx.ptr, client, _unit(unit), cond, width, _addr(d_in),
                                            _addr(d_out), n, _stream(stream)),
            "ce_unit_eval_device_width")
+
+
+def ce_unit_eval(ctx: Context, client: int, unit, inp, out=None, cond: int = 0, width: int = 16):
+    """Host buffers: inp [n][n_inputs][501] uint32 (numpy, e.g. a view of pinned
+    memory), out [n][n_outputs][501] (allocated if None)."""
+    inp = _host(inp)
+    info = ce_unit_info(unit, cond, width)
+    n = inp.size // (info["n_inputs"] * LWE_WORDS)
+    if out is None:
+        out = np.empty((n, info["n_outputs"], LWE_WORDS), np.uint32)
+    _check(lib().ce_unit_eval(ctx.ptr, client, _unit(unit), cond, width, inp.ctypes.data,
+                              out.ctypes.data, n), "ce_unit_eval")
+    return out
 
 
 def ce_set_unit_graphs(ctx: Context, on: bool):

@@ -33,10 +33,8 @@ def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     cmd = [NVCC, "-c", os.path.join(CSRC, src), "-o", obj, "-O3", "-std=c++17", "-lineinfo",
            "-Xcompiler", "-fPIC,-O2,-ffp-contract=off", "-I", INCLUDE] + ARCH
-    if src.endswith(".cu"):
-        cmd += ["-Xptxas", "-v"] if verbose else []
-    else:
-        cmd += ["-x", "cu"] if False else []
+    if src.endswith(".cu") and verbose:
+        cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -23,6 +24,22 @@ constexpr uint64_t kMaxSelftestWaitNs = 2000000000ull;
 ce_status set_error(ce_status code, const std::string &msg) {
   g_last_error = msg;
   return code;
+}
+
+namespace {
+std::atomic<uint64_t> g_dev_allocs{0}, g_dev_frees{0};
+}  // namespace
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) g_dev_allocs.fetch_add(1, std::memory_order_relaxed);
+  return e;
+}
+
+void dev_free(void *p) {
+  if (!p) return;
+  cudaFree(p);
+  g_dev_frees.fetch_add(1, std::memory_order_relaxed);
 }
 
 // Per-thread twist factors of the two-prime transform (rns_ntt.cuh) with
@@ -68,11 +85,11 @@ namespace {
 ce_status ensure_tt_digits(ce_ctx *ctx, size_t jobs) {
   if (ctx->cfg_xp != 1 || (ctx->tt_digits && jobs <= ctx->tt_cap)) return CE_OK;
   const size_t cap = std::max(jobs, ctx->job_cap);
-  cudaFree(ctx->tt_digits);
+  dev_free(ctx->tt_digits);
   ctx->tt_digits = nullptr;
   ctx->tt_cap = 0;
   ++ctx->scratch_gen;
-  if (cudaMalloc(&ctx->tt_digits, blind_rotate_tc_digit_bytes(cap)) != cudaSuccess)
+  if (dev_malloc(&ctx->tt_digits, blind_rotate_tc_digit_bytes(cap)) != cudaSuccess)
     return set_error(CE_ENOMEM, "digit operand allocation failed");
   ctx->tt_cap = cap;
   return CE_OK;
@@ -82,19 +99,19 @@ ce_status ensure_jobs(ce_ctx *ctx, size_t jobs) {
   if (jobs <= ctx->job_cap) return ensure_tt_digits(ctx, jobs);
   size_t cap = ctx->job_cap ? ctx->job_cap : 64;
   while (cap < jobs) cap *= 2;
-  cudaFree(ctx->abar);  // synchronises with work still using the old scratch
-  cudaFree(ctx->acc);
-  cudaFree(ctx->ksh);
+  dev_free(ctx->abar);  // synchronises with work still using the old scratch
+  dev_free(ctx->acc);
+  dev_free(ctx->ksh);
   ctx->abar = nullptr;
   ctx->acc = nullptr;
   ctx->ksh = nullptr;
   ctx->job_cap = 0;
   ++ctx->scratch_gen;  // captured graphs that baked in the old pointers are stale
-  cudaError_t e = cudaMalloc(&ctx->abar, cap * kAbarStride * sizeof(uint16_t));
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->acc, cap * 2 * kRingN * sizeof(uint32_t));
+  cudaError_t e = dev_malloc(&ctx->abar, cap * kAbarStride * sizeof(uint16_t));
+  if (e == cudaSuccess) e = dev_malloc(&ctx->acc, cap * 2 * kRingN * sizeof(uint32_t));
   // rounded coefficients of the tensor-core key switch: [1024][ksh_ld] (an
   // engine tick pads its outputs to tiles of 16 beyond its jobs)
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->ksh, size_t(kRingN) * ksh_ld(cap) * sizeof(uint16_t));
+  if (e == cudaSuccess) e = dev_malloc(&ctx->ksh, size_t(kRingN) * ksh_ld(cap) * sizeof(uint16_t));
   if (e != cudaSuccess) return set_error(CE_ENOMEM, "scratch allocation failed");
   ctx->job_cap = cap;
   return ensure_tt_digits(ctx, cap);
@@ -104,18 +121,18 @@ ce_status ensure_io(ce_ctx *ctx, size_t n) {
   if (n <= ctx->io_cap) return CE_OK;
   size_t cap = ctx->io_cap ? ctx->io_cap : 64;
   while (cap < n) cap *= 2;
-  cudaFree(ctx->io_ops);
-  cudaFree(ctx->io_a);
-  cudaFree(ctx->io_b);
-  cudaFree(ctx->io_out);
+  dev_free(ctx->io_ops);
+  dev_free(ctx->io_a);
+  dev_free(ctx->io_b);
+  dev_free(ctx->io_out);
   ctx->io_ops = nullptr;
   ctx->io_a = ctx->io_b = ctx->io_out = nullptr;
   ctx->io_cap = 0;
   const size_t w = cap * kLweWords * sizeof(uint32_t);
-  cudaError_t e = cudaMalloc(&ctx->io_ops, cap);
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->io_a, w);
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->io_b, w);
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->io_out, w);
+  cudaError_t e = dev_malloc(&ctx->io_ops, cap);
+  if (e == cudaSuccess) e = dev_malloc(&ctx->io_a, w);
+  if (e == cudaSuccess) e = dev_malloc(&ctx->io_b, w);
+  if (e == cudaSuccess) e = dev_malloc(&ctx->io_out, w);
   if (e != cudaSuccess) return set_error(CE_ENOMEM, "staging allocation failed");
   ctx->io_cap = cap;
   return CE_OK;
@@ -235,6 +252,10 @@ ce_status run_path(ce_ctx *ctx, Client *cl, int mode, const uint8_t *ops, const 
   return CE_OK;
 }
 
+}  // namespace
+
+namespace ce {
+
 ce_status check_device_error(ce_ctx *ctx) {
   int h = 0;
   cudaError_t e = cudaMemcpy(&h, ctx->err, sizeof(int), cudaMemcpyDeviceToHost);
@@ -247,9 +268,14 @@ ce_status check_device_error(ce_ctx *ctx) {
   return CE_OK;
 }
 
-}  // namespace
+}  // namespace ce
 
 extern "C" const char *ce_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" void ce_device_alloc_count(uint64_t *allocations, uint64_t *frees) {
+  if (allocations) *allocations = g_dev_allocs.load();
+  if (frees) *frees = g_dev_frees.load();
+}
 
 extern "C" uint64_t ce_client_footprint_bytes(void) { return kClientBytes; }
 
@@ -272,11 +298,12 @@ extern "C" ce_status ce_create(ce_ctx **out, int device, uint64_t hbm_budget_byt
   ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : uint64_t(free_b) / 10 * 9;
   std::vector<uint4> tw(kTwistEntries);
   transform_tables(tw.data());
-  e = cudaMalloc(&ctx->tw, kTwistEntries * sizeof(uint4));
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->err, sizeof(int));
+  e = dev_malloc(&ctx->tw, kTwistEntries * sizeof(uint4));
+  if (e == cudaSuccess) e = dev_malloc(&ctx->err, sizeof(int));
   if (e == cudaSuccess)
     e = cudaMemcpy(ctx->tw, tw.data(), kTwistEntries * sizeof(uint4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(ctx->err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->order_ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     ce_destroy(ctx);
     return cuda_fail(e, "ce_create");
@@ -288,25 +315,24 @@ extern "C" ce_status ce_create(ce_ctx **out, int device, uint64_t hbm_budget_byt
 extern "C" void ce_destroy(ce_ctx *ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
-  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  else cudaDeviceSynchronize();
+  cudaDeviceSynchronize();  // work may be in flight on callers' streams
   for (auto &c : ctx->clients) {
-    cudaFree(c.bsk);
-    cudaFree(c.ksk);
-    cudaFree(c.ksk_planes);
-    cudaFree(c.bsk_coef);
-    cudaFree(c.bsk_hankel);
+    dev_free(c.bsk);
+    dev_free(c.ksk);
+    dev_free(c.ksk_planes);
+    dev_free(c.bsk_coef);
+    dev_free(c.bsk_hankel);
   }
-  cudaFree(ctx->tw);
-  cudaFree(ctx->tt_digits);
-  cudaFree(ctx->ksh);
-  cudaFree(ctx->err);
-  cudaFree(ctx->abar);
-  cudaFree(ctx->acc);
-  cudaFree(ctx->io_ops);
-  cudaFree(ctx->io_a);
-  cudaFree(ctx->io_b);
-  cudaFree(ctx->io_out);
+  dev_free(ctx->tw);
+  dev_free(ctx->tt_digits);
+  dev_free(ctx->ksh);
+  dev_free(ctx->err);
+  dev_free(ctx->abar);
+  dev_free(ctx->acc);
+  dev_free(ctx->io_ops);
+  dev_free(ctx->io_a);
+  dev_free(ctx->io_b);
+  dev_free(ctx->io_out);
   engine_destroy(ctx->engine);
   ctx->engine = nullptr;
   for (auto &t : ctx->timed) {
@@ -314,6 +340,7 @@ extern "C" void ce_destroy(ce_ctx *ctx) {
     cudaEventDestroy(t.b);
   }
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->order_ev) cudaEventDestroy(ctx->order_ev);
   delete ctx;
 }
 
@@ -323,20 +350,21 @@ extern "C" ce_status ce_client_admit(ce_ctx *ctx, const void *cloud_key, size_t 
   const uint32_t *w = static_cast<const uint32_t *>(cloud_key);
   if (bytes != CE_CLOUD_BYTES || w[0] != 0x4B434543u || w[1] != 1u)
     return set_error(CE_EINVAL, "ce_client_admit: not a cloud key");
+  std::lock_guard<std::recursive_mutex> lock(ctx->mu);
   if (ctx->used + kClientBytes > ctx->budget)
     return set_error(CE_EADMIT, "ce_client_admit: over the HBM budget");
   cudaSetDevice(ctx->device);
   Client cl;
   uint32_t *coef = nullptr;
-  cudaError_t e = cudaMalloc(&cl.bsk, kBskNttBytes);
-  if (e == cudaSuccess) e = cudaMalloc(&cl.ksk, kKskDevBytes);
-  if (e == cudaSuccess) e = cudaMalloc(&cl.ksk_planes, kKsPlaneBytes);
-  if (e == cudaSuccess) e = cudaMalloc(&coef, size_t(CE_BSK_WORDS) * 4);
+  cudaError_t e = dev_malloc(&cl.bsk, kBskNttBytes);
+  if (e == cudaSuccess) e = dev_malloc(&cl.ksk, kKskDevBytes);
+  if (e == cudaSuccess) e = dev_malloc(&cl.ksk_planes, kKsPlaneBytes);
+  if (e == cudaSuccess) e = dev_malloc(&coef, size_t(CE_BSK_WORDS) * 4);
   if (e != cudaSuccess) {
-    cudaFree(cl.bsk);
-    cudaFree(cl.ksk);
-    cudaFree(cl.ksk_planes);
-    cudaFree(coef);
+    dev_free(cl.bsk);
+    dev_free(cl.ksk);
+    dev_free(cl.ksk_planes);
+    dev_free(coef);
     return set_error(CE_ENOMEM, "ce_client_admit: device allocation failed");
   }
   const uint32_t *bsk = w + 2;
@@ -358,10 +386,10 @@ extern "C" ce_status ce_client_admit(ce_ctx *ctx, const void *cloud_key, size_t 
   if (e == cudaSuccess) e = launch_ksk_to_planes(cl.ksk, cl.ksk_planes, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
-    cudaFree(cl.bsk);
-    cudaFree(cl.ksk);
-    cudaFree(cl.ksk_planes);
-    cudaFree(coef);
+    dev_free(cl.bsk);
+    dev_free(cl.ksk);
+    dev_free(cl.ksk_planes);
+    dev_free(coef);
     return cuda_fail(e, "ce_client_admit");
   }
   cl.bsk_coef = coef;
@@ -372,11 +400,14 @@ extern "C" ce_status ce_client_admit(ce_ctx *ctx, const void *cloud_key, size_t 
       id = int(i);
       break;
     }
-  if (id < 0) {
-    id = int(ctx->clients.size());
-    ctx->clients.push_back(cl);
-  } else {
-    ctx->clients[id] = cl;
+  {
+    std::lock_guard<std::mutex> cl_lock(ctx->clients_mu);
+    if (id < 0) {
+      id = int(ctx->clients.size());
+      ctx->clients.push_back(cl);
+    } else {
+      ctx->clients[id] = cl;
+    }
   }
   ctx->used += kClientBytes;
   *client_id = id;
@@ -385,18 +416,23 @@ extern "C" ce_status ce_client_admit(ce_ctx *ctx, const void *cloud_key, size_t 
 
 extern "C" ce_status ce_client_evict(ce_ctx *ctx, int client_id) {
   if (!ctx) return set_error(CE_EINVAL, "ce_client_evict: null context");
+  std::lock_guard<std::recursive_mutex> lock(ctx->mu);
+  std::lock_guard<std::mutex> cl_lock(ctx->clients_mu);
   Client *cl = find_client(ctx, client_id);
   if (!cl) return set_error(CE_ENOTFOUND, "ce_client_evict: unknown client");
+  for (ce_server *s : ctx->servers)
+    if (server_client_busy(s, client_id))
+      return set_error(CE_EINVAL, "ce_client_evict: the client has requests queued or running "
+                                  "on a serving loop");
   cudaSetDevice(ctx->device);
-  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  else cudaDeviceSynchronize();
+  cudaDeviceSynchronize();  // its keys may be in use on any stream
   engine_drop_client(ctx->engine, client_id);
-  cudaFree(cl->bsk);
-  cudaFree(cl->ksk);
-  cudaFree(cl->ksk_planes);
-  cudaFree(cl->bsk_coef);
+  dev_free(cl->bsk);
+  dev_free(cl->ksk);
+  dev_free(cl->ksk_planes);
+  dev_free(cl->bsk_coef);
   if (cl->bsk_hankel) {
-    cudaFree(cl->bsk_hankel);
+    dev_free(cl->bsk_hankel);
     ctx->used -= blind_rotate_tc_key_bytes();
   }
   *cl = Client();
@@ -410,9 +446,10 @@ extern "C" ce_status ce_gates_batch_device(ce_ctx *ctx, int client, const uint8_
   if (!ctx) return set_error(CE_EINVAL, "ce_gates_batch_device: null context");
   if (n && (!d_ops || !d_a || !d_b || !d_out))
     return set_error(CE_EINVAL, "ce_gates_batch_device: null buffer");
+  cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
+  CtxWork work(ctx, st);
   Client *cl = find_client(ctx, client);
   if (!cl) return set_error(CE_ENOTFOUND, "ce_gates_batch_device: unknown client");
-  cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
   return run_path(ctx, cl, 0, d_ops, d_a, d_b, nullptr, d_out, n, st);
 }
 
@@ -422,9 +459,10 @@ extern "C" ce_status ce_mux_batch_device(ce_ctx *ctx, int client, const uint32_t
   if (!ctx) return set_error(CE_EINVAL, "ce_mux_batch_device: null context");
   if (n && (!d_a || !d_b || !d_c || !d_out))
     return set_error(CE_EINVAL, "ce_mux_batch_device: null buffer");
+  cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
+  CtxWork work(ctx, st);
   Client *cl = find_client(ctx, client);
   if (!cl) return set_error(CE_ENOTFOUND, "ce_mux_batch_device: unknown client");
-  cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
   return run_path(ctx, cl, 1, nullptr, d_a, d_b, d_c, d_out, n, st);
 }
 
@@ -435,12 +473,13 @@ extern "C" ce_status ce_gates_batch(ce_ctx *ctx, int client, const uint8_t *ops,
   if (!ops || !a || !b || !out) return set_error(CE_EINVAL, "ce_gates_batch: null buffer");
   for (size_t i = 0; i < n; ++i)
     if (ops[i] > CE_ORYN) return set_error(CE_EINVAL, "ce_gates_batch: bad gate opcode");
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = ctx->stream;
+  CtxWork work(ctx, st);
   Client *cl = find_client(ctx, client);
   if (!cl) return set_error(CE_ENOTFOUND, "ce_gates_batch: unknown client");
-  cudaSetDevice(ctx->device);
   ce_status s = ensure_io(ctx, n);
   if (s != CE_OK) return s;
-  cudaStream_t st = ctx->stream;
   const size_t w = n * kLweWords * sizeof(uint32_t);
   cudaError_t e = cudaMemcpyAsync(ctx->io_ops, ops, n, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->io_a, a, w, cudaMemcpyHostToDevice, st);
@@ -477,6 +516,7 @@ extern "C" ce_status ce_negacyclic_mul_device(ce_ctx *ctx, const int16_t *d_d,
 extern "C" ce_status ce_set_blind_rotate_config(ce_ctx *ctx, int gates_per_block,
                                                 int blocks_per_sm) {
   if (!ctx) return set_error(CE_EINVAL, "ce_set_blind_rotate_config: null context");
+  std::lock_guard<std::recursive_mutex> lock(ctx->mu);
   if (gates_per_block < 0 || gates_per_block > 4)
     return set_error(CE_EINVAL, "gates_per_block must be 0 (auto), 1, 2, 3 (one gate, three "
                                 "groups) or 4");
@@ -490,6 +530,7 @@ extern "C" ce_status ce_set_blind_rotate_config(ce_ctx *ctx, int gates_per_block
 
 extern "C" ce_status ce_set_keyswitch_config(ce_ctx *ctx, int engine) {
   if (!ctx) return set_error(CE_EINVAL, "ce_set_keyswitch_config: null context");
+  std::lock_guard<std::recursive_mutex> lock(ctx->mu);
   if (engine < 0 || engine > 2)
     return set_error(CE_EINVAL, "key-switch engine must be 0 (auto), 1 (CUDA cores) or 2 "
                                 "(tensor cores)");
@@ -499,6 +540,7 @@ extern "C" ce_status ce_set_keyswitch_config(ce_ctx *ctx, int engine) {
 
 extern "C" ce_status ce_set_external_product_form(ce_ctx *ctx, int form) {
   if (!ctx) return set_error(CE_EINVAL, "ce_set_external_product_form: null context");
+  std::lock_guard<std::recursive_mutex> lock(ctx->mu);
   if (form < 0 || form > 1)
     return set_error(CE_EINVAL, "external-product form must be 0 (transform, CUDA cores) or 1 "
                                 "(Toeplitz, tensor cores)");
@@ -527,6 +569,7 @@ extern "C" ce_status ce_selftest_device_wait(ce_ctx *ctx, uint64_t limit_ns) {
 
 extern "C" ce_status ce_profile_enable(ce_ctx *ctx, int on) {
   if (!ctx) return set_error(CE_EINVAL, "ce_profile_enable: null context");
+  std::lock_guard<std::recursive_mutex> lock(ctx->mu);
   ctx->profile = on != 0;
   return CE_OK;
 }
@@ -534,6 +577,7 @@ extern "C" ce_status ce_profile_enable(ce_ctx *ctx, int on) {
 extern "C" ce_status ce_profile_read(ce_ctx *ctx, double *ms, int *launches, int kinds) {
   if (!ctx || !ms || !launches || kinds <= 0)
     return set_error(CE_EINVAL, "ce_profile_read: bad argument");
+  std::lock_guard<std::recursive_mutex> lock(ctx->mu);
   for (int k = 0; k < kinds; ++k) {
     ms[k] = 0.0;
     launches[k] = 0;
@@ -599,14 +643,14 @@ ce_status ensure_hankel(ce_ctx *ctx, Client *cl) {
   const uint64_t bytes = blind_rotate_tc_key_bytes();
   if (ctx->used + bytes > ctx->budget)
     return set_error(CE_EADMIT, "tensor-core external product: key over the HBM budget");
-  if (cudaMalloc(&cl->bsk_hankel, bytes) != cudaSuccess) {
+  if (dev_malloc(&cl->bsk_hankel, bytes) != cudaSuccess) {
     cl->bsk_hankel = nullptr;
     return set_error(CE_ENOMEM, "tensor-core external product: key allocation failed");
   }
   cudaError_t e = launch_bsk_to_hankel(cl->bsk_coef, cl->bsk_hankel, ctx->stream);
   if (e == cudaSuccess) e = ctx->stream ? cudaStreamSynchronize(ctx->stream) : cudaDeviceSynchronize();
   if (e != cudaSuccess) {
-    cudaFree(cl->bsk_hankel);
+    dev_free(cl->bsk_hankel);
     cl->bsk_hankel = nullptr;
     return cuda_error(e, "bsk_to_hankel");
   }
@@ -643,6 +687,7 @@ cudaEvent_t take_event(ce_ctx *ctx) {
 extern "C" ce_status ce_autotune(ce_ctx *ctx, int client, int *out_jobs, int *out_g, int cap,
                                  int *count) {
   if (!ctx) return set_error(CE_EINVAL, "ce_autotune: null context");
+  CtxWork work(ctx, ctx->stream);
   Client *cl = find_client(ctx, client);
   if (!cl) return set_error(CE_ENOTFOUND, "ce_autotune: unknown client");
   const int ladder[] = {1, 8, 38, 76, 152, 304, 608, 1216, 2432, 4864, 9728};

@@ -1,6 +1,9 @@
 // Internal definitions shared by the library's translation units.
 #pragma once
 
+#include <cuda_runtime.h>
+
+#include <cstddef>
 #include <cstdint>
 #include <string>
 
@@ -34,5 +37,13 @@ constexpr int kChunkWords = 4 * 8 * 128;                  // 4096 uint64 = 32 KB
 constexpr uint64_t kBskNttWords = uint64_t(kLweN) * kGadgetL * kChunkWords;
 
 ce_status set_error(ce_status code, const std::string &msg);
+
+// Device allocations of the library, counted (ce_device_alloc_count).
+cudaError_t dev_malloc(void **p, size_t bytes);
+template <class T>
+cudaError_t dev_malloc(T **p, size_t bytes) {
+  return dev_malloc(reinterpret_cast<void **>(p), bytes);
+}
+void dev_free(void *p);
 
 }  // namespace ce

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -34,7 +35,19 @@ class Engine;  // netlist engine (engine.cu), created on first use
 
 }  // namespace ce
 
+struct ce_server;
+
 struct ce_ctx {
+  // Host threads that enqueue work on the context (API calls and the worker
+  // of a serving loop) take this lock; their GPU work is ordered through
+  // order_ev (see ce::CtxWork).
+  std::recursive_mutex mu;
+  cudaEvent_t order_ev = nullptr;
+  bool order_recorded = false;
+  std::vector<ce_server *> servers;  // live serving loops on this context
+  // Guards the structure of `clients` for readers that do not take `mu`
+  // (request submission); writers hold both.
+  std::mutex clients_mu;
   int device = 0;
   cudaStream_t stream = nullptr;
   int sms = 0;
@@ -90,6 +103,43 @@ void engine_drop_client(Engine *e, int client);
 // while profiling is on, else nullptr; keep_mma_events files them.
 cudaEvent_t *mma_events(ce_ctx *ctx);
 void keep_mma_events(ce_ctx *ctx);
+// One call that enqueues GPU work on `st` using the context's shared state
+// (scratch, engine arena, keys): holds the context lock for the call and
+// orders the call's GPU work after the previous such call's, whatever stream
+// that one used (a serving loop's worker enqueues on its own stream).  While
+// `st` is being captured into a CUDA graph no ordering is added (an event
+// recorded outside a capture cannot be waited on inside it).
+class CtxWork {
+ public:
+  CtxWork(ce_ctx *c, cudaStream_t st) : ctx_(c), lock_(c->mu), st_(st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    capturing_ = cs != cudaStreamCaptureStatusNone;
+    if (!capturing_ && ctx_->order_ev && ctx_->order_recorded)
+      cudaStreamWaitEvent(st, ctx_->order_ev, 0);
+  }
+  ~CtxWork() {
+    if (capturing_ || !ctx_->order_ev) return;
+    if (cudaEventRecord(ctx_->order_ev, st_) == cudaSuccess) ctx_->order_recorded = true;
+  }
+  CtxWork(const CtxWork &) = delete;
+  CtxWork &operator=(const CtxWork &) = delete;
+
+ private:
+  ce_ctx *ctx_;
+  std::lock_guard<std::recursive_mutex> lock_;
+  cudaStream_t st_;
+  bool capturing_ = false;
+};
+
+// Reads and clears the context's device error flag (CE_ETIMEOUT for an
+// expired bounded wait, CE_EINVAL for a bad device opcode).
+ce_status check_device_error(ce_ctx *ctx);
+
+// True while a serving loop on the context has a request of `client`
+// queued or in flight (serve.cu).
+bool server_client_busy(ce_server *s, int client);
+
 template <class F>
 cudaError_t timed(ce_ctx *ctx, int kind, cudaStream_t st, F launch) {
   if (!ctx->profile) return launch();

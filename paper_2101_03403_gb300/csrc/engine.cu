@@ -33,6 +33,8 @@
 
 namespace ce {
 
+static_assert(sizeof(ce_trace_rec) == 8048, "trace record layout");
+
 namespace {
 
 constexpr uint32_t kSlotFalse = 0;  // the trivial ciphertext (0, -1/8)
@@ -61,6 +63,45 @@ __global__ void copy_out_kernel(const uint32_t *__restrict__ map, const uint32_t
   for (int m = threadIdx.x; m < kLweWords; m += blockDim.x) {
     const uint32_t v = arena[size_t(slot) * kSlotWords + m];
     out[c * kLweWords + m] = neg ? 0u - v : v;
+  }
+}
+
+// Gate trace: block r records sample r of a tick, the output at position
+// floor(r * n_outs / samples) (padding outputs are skipped): the gate's
+// operation, negation flags, client, its input slots' words and its output
+// slot's words, copied after the tick's key switch on the same stream.
+__global__ void trace_kernel(const GateJob *__restrict__ jobs, const GateOut *__restrict__ outs,
+                             int n_outs, int samples, const uint32_t *__restrict__ arena,
+                             ce_trace_rec *__restrict__ rec, unsigned long long *__restrict__ count,
+                             unsigned long long cap, uint32_t tick) {
+  const int k = int((long long)blockIdx.x * n_outs / samples);
+  const GateOut o = outs[k];
+  if (o.slot == kSlotSink) return;
+  __shared__ unsigned long long idx;
+  if (threadIdx.x == 0) idx = atomicAdd(count, 1ull);
+  __syncthreads();
+  if (idx >= cap) return;
+  ce_trace_rec &R = rec[idx];
+  const GateJob J1 = jobs[o.job1];
+  const bool mux = o.job2 >= 0;
+  const GateJob J2 = mux ? jobs[o.job2] : J1;
+  if (threadIdx.x == 0) {
+    R.op = mux ? 10 : J1.op;
+    R.neg[0] = J1.neg_a;
+    R.neg[1] = J1.neg_b;
+    R.neg[2] = mux ? J2.neg_b : 0;
+    R.client = int32_t(o.pad);
+    R.tick = tick;
+    R.index = uint32_t(k);
+    R.pad = 0;
+  }
+  const uint32_t src[4] = {J1.a, J1.b, mux ? J2.b : kSlotFalse, o.slot};
+  for (int m = threadIdx.x; m < 4 * kLweWords; m += blockDim.x) {
+    const int w = m / kLweWords, j = m % kLweWords;
+    const uint32_t v = (w == 2 && !mux) ? 0u : arena[size_t(src[w]) * kSlotWords + j];
+    uint32_t *dst = w == 3 ? reinterpret_cast<uint32_t *>(&R.out)
+                           : reinterpret_cast<uint32_t *>(&R.in[w]);
+    dst[j] = v;
   }
 }
 
@@ -128,10 +169,14 @@ class Engine {
     for (auto &p : plans) drop_plan(*p);
     for (int i = 0; i < 2; ++i) {
       if (h_desc[i]) cudaFreeHost(h_desc[i]);
-      cudaFree(d_desc[i]);
+      dev_free(d_desc[i]);
       if (desc_ev[i]) cudaEventDestroy(desc_ev[i]);
     }
-    cudaFree(arena);
+    dev_free(arena);
+    dev_free(trace_rec);
+    dev_free(trace_count);
+    dev_free(io_in);
+    dev_free(io_out);
     if (cap_stream) cudaStreamDestroy(cap_stream);
   }
 
@@ -154,14 +199,14 @@ class Engine {
     size_t ncap = cap ? cap : 1;
     while (ncap < slots) ncap *= 2;
     uint32_t *na = nullptr;
-    cudaError_t e = cudaMalloc(&na, ncap * kSlotWords * sizeof(uint32_t));
+    cudaError_t e = dev_malloc(&na, ncap * kSlotWords * sizeof(uint32_t));
     if (e != cudaSuccess) return set_error(CE_ENOMEM, "engine: arena allocation failed");
     if (arena) {
       // rare: wait for all work that may touch the old arena, then move it
       e = cudaDeviceSynchronize();
       if (e == cudaSuccess)
         e = cudaMemcpy(na, arena, cap * kSlotWords * sizeof(uint32_t), cudaMemcpyDeviceToDevice);
-      cudaFree(arena);
+      dev_free(arena);
       // plans captured the old address
       for (auto &p : plans) drop_graph(*p);
     }
@@ -289,6 +334,7 @@ class Engine {
           const SRef a = resolve(in, x.a), b = resolve(in, x.b);
           GateOut o{};
           o.slot = slot;
+          o.pad = uint32_t(client);  // read by the gate trace
           o.job1 = int32_t(t.jobs.size());
           if (x.op == kOpMux) {
             const SRef c = resolve(in, x.c);
@@ -344,12 +390,12 @@ class Engine {
     if (e != cudaSuccess) return cuda_error(e, "engine stage");
     if (off > desc_cap[b]) {
       if (h_desc[b]) cudaFreeHost(h_desc[b]);
-      cudaFree(d_desc[b]);
+      dev_free(d_desc[b]);
       h_desc[b] = nullptr;
       d_desc[b] = nullptr;
       size_t c = std::max<size_t>(off, 1 << 16) * 2;
       e = cudaMallocHost(&h_desc[b], c);
-      if (e == cudaSuccess) e = cudaMalloc(&d_desc[b], c);
+      if (e == cudaSuccess) e = dev_malloc(&d_desc[b], c);
       if (e != cudaSuccess) {
         desc_cap[b] = 0;
         return set_error(CE_ENOMEM, "engine: descriptor buffers");
@@ -415,6 +461,14 @@ class Engine {
     }
     if (e != cudaSuccess) return cuda_error(e, "engine level launch");
     *launches += 3 + (split > 1 ? 1 : 0);
+    if (trace_per_tick > 0) {
+      const int samples = std::min(trace_per_tick, n_outs);
+      trace_kernel<<<unsigned(samples), 256, 0, st>>>(jobs, outs, n_outs, samples, arena, trace_rec,
+                                                       trace_count, trace_cap, trace_tick++);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_error(e, "gate trace");
+      ++*launches;
+    }
     return CE_OK;
   }
 
@@ -443,7 +497,7 @@ class Engine {
   }
   void drop_plan(Plan &p) {
     drop_graph(p);
-    cudaFree(p.d_desc);
+    dev_free(p.d_desc);
     p.d_desc = nullptr;
     for (uint32_t sl : p.slots) unref(SRef{sl, false});
     p.slots.clear();
@@ -543,7 +597,7 @@ class Engine {
       }
     }
     p->map_off = put(map.data(), map.size() * sizeof(uint32_t));
-    cudaError_t e = cudaMalloc(&p->d_desc, blob.size());
+    cudaError_t e = dev_malloc(&p->d_desc, blob.size());
     if (e == cudaSuccess)
       e = cudaMemcpy(p->d_desc, blob.data(), blob.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_error(e, "engine plan upload");
@@ -584,7 +638,7 @@ class Engine {
     Plan *p;
     ce_status s = make_plan(unit, cond, width, client, n, d_in, d_out, &p);
     if (s != CE_OK) return s;
-    if (!use_graphs || ctx->profile) return run_plan(*p, st, launches);
+    if (!use_graphs || ctx->profile || trace_per_tick > 0) return run_plan(*p, st, launches);
     s = ensure_job_scratch(ctx, p->max_jobs);
     if (s != CE_OK) return s;
     if (p->exec && p->exec_gen != ctx->scratch_gen) drop_graph(*p);  // scratch was replaced
@@ -626,6 +680,34 @@ class Engine {
   uint64_t use_clock = 0;
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;
+  // staging buffers of ce_unit_eval (host-buffer calls), grown on demand
+  uint32_t *io_in = nullptr, *io_out = nullptr;
+  size_t io_in_cap = 0, io_out_cap = 0;
+  ce_status ensure_unit_io(size_t in_bytes, size_t out_bytes) {
+    if (in_bytes > io_in_cap) {
+      dev_free(io_in);
+      io_in = nullptr;
+      io_in_cap = 0;
+      if (dev_malloc(&io_in, in_bytes) != cudaSuccess)
+        return set_error(CE_ENOMEM, "ce_unit_eval: staging allocation failed");
+      io_in_cap = in_bytes;
+    }
+    if (out_bytes > io_out_cap) {
+      dev_free(io_out);
+      io_out = nullptr;
+      io_out_cap = 0;
+      if (dev_malloc(&io_out, out_bytes) != cudaSuccess)
+        return set_error(CE_ENOMEM, "ce_unit_eval: staging allocation failed");
+      io_out_cap = out_bytes;
+    }
+    return CE_OK;
+  }
+  // gate trace (ce_trace_enable): records of sampled gates of every tick
+  int trace_per_tick = 0;
+  ce_trace_rec *trace_rec = nullptr;
+  unsigned long long *trace_count = nullptr;
+  unsigned long long trace_cap = 0;
+  uint32_t trace_tick = 0;
   // one host thread at a time inside the engine (a serving thread and
   // register reads of other threads may meet here)
   std::recursive_mutex mu;
@@ -809,6 +891,7 @@ int gates_at_level(const Instance &in) {
 ce_status engine_serve_tick(ce_ctx *ctx, cudaStream_t st, const std::vector<int> &start_clients,
                             const std::vector<ce_insn> &start_insns, std::vector<int> &retired,
                             int *active_after, int *bootstraps) {
+  CtxWork work(ctx, st);
   Engine *E;
   ce_status s = get_engine(ctx, &E);
   if (s != CE_OK) return s;
@@ -858,6 +941,7 @@ ce_status engine_serve_tick(ce_ctx *ctx, cudaStream_t st, const std::vector<int>
 
 ce_status exec_programs(ce_ctx *ctx, size_t n_prog, const int *clients, const ce_insn *const *progs,
                         const size_t *lens, uint64_t timeout_ns, cudaStream_t st, int *ticks) {
+  CtxWork work(ctx, st);
   Engine *E;
   ce_status s = get_engine(ctx, &E);
   if (s != CE_OK) return s;
@@ -921,6 +1005,8 @@ extern "C" ce_status ce_unit_eval_device_width(ce_ctx *ctx, int client, int unit
     return set_error(CE_EINVAL, "ce_unit_eval_device: bad unit or condition");
   if (width < 2 || width > 32 || (width & (width - 1)))
     return set_error(CE_EINVAL, "ce_unit_eval_device: width must be a power of two in 2..32");
+  cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
+  CtxWork work(ctx, st);
   if (!live_client(ctx, client)) return set_error(CE_ENOTFOUND, "ce_unit_eval_device: unknown client");
   if (n == 0) {
     ctx->last_launches = 0;
@@ -931,12 +1017,50 @@ extern "C" ce_status ce_unit_eval_device_width(ce_ctx *ctx, int client, int unit
   Engine *E;
   ce_status s = get_engine(ctx, &E);
   if (s != CE_OK) return s;
-  cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
   int launches = 0;
   std::lock_guard<std::recursive_mutex> lock(E->mu);
   s = E->eval_unit(unit, cond, width, client, d_in, d_out, n, st, &launches);
   ctx->last_launches = launches;
   return s;
+}
+
+extern "C" ce_status ce_unit_eval(ce_ctx *ctx, int client, int unit, int cond, int width,
+                                  const ce_lwe *in, ce_lwe *out, size_t n) {
+  if (!ctx) return set_error(CE_EINVAL, "ce_unit_eval: null context");
+  if (unit < 0 || unit >= kUnitCount || cond < 0 || cond > 13)
+    return set_error(CE_EINVAL, "ce_unit_eval: bad unit or condition");
+  if (width < 2 || width > 32 || (width & (width - 1)))
+    return set_error(CE_EINVAL, "ce_unit_eval: width must be a power of two in 2..32");
+  if (n && (!in || !out)) return set_error(CE_EINVAL, "ce_unit_eval: null buffer");
+  if (n > (size_t(1) << 20)) return set_error(CE_EINVAL, "ce_unit_eval: n too large");
+  cudaSetDevice(ctx->device);
+  cudaStream_t st = ctx->stream;
+  CtxWork work(ctx, st);
+  if (!live_client(ctx, client)) return set_error(CE_ENOTFOUND, "ce_unit_eval: unknown client");
+  if (n == 0) {
+    ctx->last_launches = 0;
+    return CE_OK;
+  }
+  Engine *E;
+  ce_status s = get_engine(ctx, &E);
+  if (s != CE_OK) return s;
+  std::lock_guard<std::recursive_mutex> lock(E->mu);
+  const Netlist *net = E->netlist(unit, cond, width);
+  if (!net) return set_error(CE_EINVAL, "ce_unit_eval: bad unit or width");
+  const size_t in_bytes = n * net->n_inputs * sizeof(ce_lwe);
+  const size_t out_bytes = n * net->outputs.size() * sizeof(ce_lwe);
+  s = E->ensure_unit_io(in_bytes, out_bytes);
+  if (s != CE_OK) return s;
+  cudaError_t e = cudaMemcpyAsync(E->io_in, in, in_bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_error(e, "ce_unit_eval upload");
+  int launches = 0;
+  s = E->eval_unit(unit, cond, width, client, E->io_in, E->io_out, n, st, &launches);
+  if (s != CE_OK) return s;
+  ctx->last_launches = launches;
+  e = cudaMemcpyAsync(out, E->io_out, out_bytes, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(e, "ce_unit_eval");
+  return check_device_error(ctx);
 }
 
 extern "C" ce_status ce_unit_eval_device(ce_ctx *ctx, int client, int unit, int cond,
@@ -947,6 +1071,7 @@ extern "C" ce_status ce_unit_eval_device(ce_ctx *ctx, int client, int unit, int 
 
 extern "C" ce_status ce_set_unit_graphs(ce_ctx *ctx, int on) {
   if (!ctx) return set_error(CE_EINVAL, "ce_set_unit_graphs: null context");
+  std::lock_guard<std::recursive_mutex> ctx_lock(ctx->mu);
   Engine *E;
   ce_status s = get_engine(ctx, &E);
   if (s != CE_OK) return s;
@@ -956,6 +1081,7 @@ extern "C" ce_status ce_set_unit_graphs(ce_ctx *ctx, int on) {
 
 extern "C" ce_status ce_reg_write(ce_ctx *ctx, int client, int reg, const ce_lwe *bits) {
   if (!ctx || !bits || reg < 0 || reg >= kRegs) return set_error(CE_EINVAL, "ce_reg_write: bad argument");
+  CtxWork work(ctx, ctx->stream);
   if (!live_client(ctx, client)) return set_error(CE_ENOTFOUND, "ce_reg_write: unknown client");
   Engine *E;
   ce_status s = get_engine(ctx, &E);
@@ -1000,6 +1126,7 @@ static ce_status read_refs(ce_ctx *ctx, Engine *E, const SRef *refs_in, int coun
 
 extern "C" ce_status ce_reg_read(ce_ctx *ctx, int client, int reg, ce_lwe *bits) {
   if (!ctx || !bits || reg < 0 || reg >= kRegs) return set_error(CE_EINVAL, "ce_reg_read: bad argument");
+  std::lock_guard<std::recursive_mutex> ctx_lock(ctx->mu);
   if (!live_client(ctx, client)) return set_error(CE_ENOTFOUND, "ce_reg_read: unknown client");
   Engine *E;
   ce_status s = get_engine(ctx, &E);
@@ -1010,6 +1137,7 @@ extern "C" ce_status ce_reg_read(ce_ctx *ctx, int client, int reg, ce_lwe *bits)
 
 extern "C" ce_status ce_flags_read(ce_ctx *ctx, int client, ce_lwe *nzcv) {
   if (!ctx || !nzcv) return set_error(CE_EINVAL, "ce_flags_read: bad argument");
+  std::lock_guard<std::recursive_mutex> ctx_lock(ctx->mu);
   if (!live_client(ctx, client)) return set_error(CE_ENOTFOUND, "ce_flags_read: unknown client");
   Engine *E;
   ce_status s = get_engine(ctx, &E);
@@ -1032,4 +1160,66 @@ extern "C" ce_status ce_exec_multi(ce_ctx *ctx, size_t n_programs, const int *cl
     return set_error(CE_EINVAL, "ce_exec_multi: bad argument");
   int ticks = 0;
   return exec_programs(ctx, n_programs, clients, progs, lens, timeout_ns, ctx->stream, &ticks);
+}
+
+extern "C" ce_status ce_trace_enable(ce_ctx *ctx, int per_tick, size_t cap) {
+  if (!ctx) return set_error(CE_EINVAL, "ce_trace_enable: null context");
+  if (per_tick < 0 || per_tick > 4096 || (per_tick > 0 && (cap == 0 || cap > (size_t(1) << 20))))
+    return set_error(CE_EINVAL, "ce_trace_enable: per_tick must lie in 0..4096 and cap in "
+                                "1..2^20");
+  std::lock_guard<std::recursive_mutex> ctx_lock(ctx->mu);
+  Engine *E;
+  ce_status s = get_engine(ctx, &E);
+  if (s != CE_OK) return s;
+  std::lock_guard<std::recursive_mutex> lock(E->mu);
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();  // records of earlier ticks may still be in flight
+  dev_free(E->trace_rec);
+  dev_free(E->trace_count);
+  E->trace_rec = nullptr;
+  E->trace_count = nullptr;
+  E->trace_cap = 0;
+  E->trace_per_tick = 0;
+  E->trace_tick = 0;
+  if (per_tick == 0) return CE_OK;
+  cudaError_t e = dev_malloc(&E->trace_rec, cap * sizeof(ce_trace_rec));
+  if (e == cudaSuccess) e = dev_malloc(&E->trace_count, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(E->trace_count, 0, sizeof(unsigned long long));
+  if (e != cudaSuccess) {
+    dev_free(E->trace_rec);
+    dev_free(E->trace_count);
+    E->trace_rec = nullptr;
+    E->trace_count = nullptr;
+    return set_error(CE_ENOMEM, "ce_trace_enable: record buffer allocation failed");
+  }
+  E->trace_cap = cap;
+  E->trace_per_tick = per_tick;
+  return CE_OK;
+}
+
+extern "C" ce_status ce_trace_read(ce_ctx *ctx, ce_trace_rec *out, size_t cap, size_t *count,
+                                   uint64_t *seen) {
+  if (!ctx || !count || (cap && !out)) return set_error(CE_EINVAL, "ce_trace_read: bad argument");
+  std::lock_guard<std::recursive_mutex> ctx_lock(ctx->mu);
+  Engine *E;
+  ce_status s = get_engine(ctx, &E);
+  if (s != CE_OK) return s;
+  std::lock_guard<std::recursive_mutex> lock(E->mu);
+  *count = 0;
+  if (seen) *seen = 0;
+  if (!E->trace_count) return CE_OK;
+  cudaSetDevice(ctx->device);
+  unsigned long long total = 0;
+  cudaError_t e = cudaDeviceSynchronize();  // ticks may have run on any stream
+  if (e == cudaSuccess)
+    e = cudaMemcpy(&total, E->trace_count, sizeof(total), cudaMemcpyDeviceToHost);
+  const size_t stored = size_t(std::min<unsigned long long>(total, E->trace_cap));
+  const size_t n = std::min(stored, cap);
+  if (e == cudaSuccess && n)
+    e = cudaMemcpy(out, E->trace_rec, n * sizeof(ce_trace_rec), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(E->trace_count, 0, sizeof(unsigned long long));
+  if (e != cudaSuccess) return cuda_error(e, "ce_trace_read");
+  *count = n;
+  if (seen) *seen = total;
+  return CE_OK;
 }

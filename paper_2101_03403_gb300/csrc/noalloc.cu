@@ -16,6 +16,7 @@
 #include <string>
 
 #include "ce_internal.h"
+#include "ctx.h"
 #include "launch.h"
 
 namespace {
@@ -68,10 +69,15 @@ extern "C" ce_status ce_gates_batch_device_noalloc(ce_ctx *ctx, int client, cons
     return set_error(CE_EINVAL, "ce_gates_batch_device_noalloc: at most 256 gates per call");
   if (n && (!d_ops || !d_a || !d_b || !d_out))
     return set_error(CE_EINVAL, "ce_gates_batch_device_noalloc: null buffer");
+  cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : ctx->stream;
+  CtxWork work(ctx, st);  // context lock; ordered after the context's earlier work
   GatePathResources res;
   ce_status s = gate_path_resources(ctx, client, &res);
   if (s != CE_OK) return s;
-  if (n == 0) return CE_OK;
+  if (n == 0) {
+    ctx->last_launches = 0;
+    return CE_OK;
+  }
 
   int current = -1;
   cudaError_t e = cudaGetDevice(&current);
@@ -85,22 +91,30 @@ extern "C" ce_status ce_gates_batch_device_noalloc(ce_ctx *ctx, int client, cons
   if (s == CE_OK) {
     uint16_t *abar = static_cast<uint16_t *>(base);
     uint32_t *acc = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(base) + kAbarBytes);
-    cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : res.stream;
     int G, blocks, tile, jsplit;
     gate_path_shape(ctx, n, n, &G, &blocks, &tile, &jsplit);
-    e = launch_lincomb_modswitch(d_ops, d_a, d_b, nullptr, abar, int(n), 0, res.err, st);
+    // the same kinds as the allocating path, so per-kernel timing sees them
+    e = timed(ctx, 0, st, [&] {
+      return launch_lincomb_modswitch(d_ops, d_a, d_b, nullptr, abar, int(n), 0, res.err, st);
+    });
     if (e != cudaSuccess) {
       s = fail(e, "lincomb_modswitch");
-    } else if ((e = launch_blind_rotate(res.bsk, abar, acc, int(n), res.tw, res.err, G, blocks,
-                                        st)) != cudaSuccess) {
+    } else if ((e = timed(ctx, 1, st, [&] {
+                  return launch_blind_rotate(res.bsk, abar, acc, int(n), res.tw, res.err, G,
+                                             blocks, st);
+                })) != cudaSuccess) {
       s = fail(e, "blind_rotate");
     } else if (jsplit > 1 &&
                (e = cudaMemsetAsync(d_out, 0, n * kLweWords * sizeof(uint32_t), st)) !=
                    cudaSuccess) {
       s = fail(e, "memset of the output");
-    } else if ((e = launch_extract_keyswitch(acc, res.ksk, d_out, int(n), false, tile, jsplit,
-                                             st)) != cudaSuccess) {
+    } else if ((e = timed(ctx, 2, st, [&] {
+                  return launch_extract_keyswitch(acc, res.ksk, d_out, int(n), false, tile,
+                                                  jsplit, st);
+                })) != cudaSuccess) {
       s = fail(e, "extract_keyswitch");
+    } else {
+      ctx->last_launches = 3;
     }
   }
   if (current != res.device) cudaSetDevice(current);

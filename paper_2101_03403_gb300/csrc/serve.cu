@@ -12,6 +12,7 @@
 // the CUDA event recorded after its last tick has completed.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -189,6 +190,18 @@ void serve_loop(ce_server *s) {
 
 }  // namespace
 
+namespace ce {
+
+bool server_client_busy(ce_server *s, int client) {
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (s->running.count(client)) return true;
+  for (uint64_t id : s->queue)
+    if (s->tickets[id].client == client) return true;
+  return false;
+}
+
+}  // namespace ce
+
 extern "C" ce_status ce_server_create(ce_ctx *ctx, int max_inflight, ce_server **out) {
   if (!ctx || !out) return set_error(CE_EINVAL, "ce_server_create: bad argument");
   ce_server *s = new ce_server();
@@ -200,6 +213,10 @@ extern "C" ce_status ce_server_create(ce_ctx *ctx, int max_inflight, ce_server *
     delete s;
     return cuda_error(e, "ce_server_create");
   }
+  {
+    std::lock_guard<std::recursive_mutex> lock(ctx->mu);
+    ctx->servers.push_back(s);
+  }
   s->worker = std::thread(serve_loop, s);
   *out = s;
   return CE_OK;
@@ -208,10 +225,13 @@ extern "C" ce_status ce_server_create(ce_ctx *ctx, int max_inflight, ce_server *
 extern "C" ce_status ce_server_submit(ce_server *s, int client, const ce_insn *insn,
                                       uint64_t *ticket) {
   if (!s || !insn || !ticket) return set_error(CE_EINVAL, "ce_server_submit: bad argument");
+  if (insn->op > CE_I_SUBS || insn->rd > 7 || insn->rn > 7 || insn->rm > 7 || insn->cond > 13)
+    return set_error(CE_EINVAL, "ce_server_submit: malformed instruction");
+  // the client stays admitted while its ticket is queued: eviction checks
+  // the queue under the same lock
+  std::lock_guard<std::mutex> cl_lock(s->ctx->clients_mu);
   if (client < 0 || client >= int(s->ctx->clients.size()) || !s->ctx->clients[client].live)
     return set_error(CE_ENOTFOUND, "ce_server_submit: unknown client");
-  if (insn->op > 11 || insn->rd > 7 || insn->rn > 7 || insn->rm > 7 || insn->cond > 13)
-    return set_error(CE_EINVAL, "ce_server_submit: malformed instruction");
   {
     std::lock_guard<std::mutex> lock(s->mu);
     if (s->fatal != CE_OK) return set_error(s->fatal, "ce_server_submit: server failed");
@@ -280,6 +300,11 @@ extern "C" void ce_server_destroy(ce_server *s) {
   if (s->worker.joinable()) s->worker.join();
   reap(s, true);
   cudaStreamSynchronize(s->stream);
+  {
+    std::lock_guard<std::recursive_mutex> lock(s->ctx->mu);
+    auto &v = s->ctx->servers;
+    v.erase(std::remove(v.begin(), v.end(), s), v.end());
+  }
   for (auto e : s->ev_free) cudaEventDestroy(e);
   cudaStreamDestroy(s->stream);
   delete s;

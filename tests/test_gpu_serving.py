@@ -6,7 +6,6 @@ import numpy as np
 import pytest
 
 from gpu_common import MASTER_SEED, ce, ctx, keys  # noqa: F401
-from oracle import netlists as NL
 
 pytestmark = pytest.mark.gpu
 W = 16
@@ -124,3 +123,29 @@ def test_admission_by_hbm_budget(ce, keys):
         assert ei.value.code == -3
     finally:
         small.close()
+
+
+def test_evict_refused_while_requests_pending(ce, ctx):
+    """Evicting a client whose request a serving loop still holds is refused
+    on the host (CE_EINVAL) before anything is freed; once the request is
+    done the eviction goes through."""
+    c, _ = ctx
+    seed = MASTER_SEED + 300
+    sk = ce.ce_secret_keygen(seed)
+    cid = ce.ce_client_admit(c, ce.ce_cloud_keygen(sk, seed))
+    ce.ce_reg_write(c, cid, 0, enc_word(ce, sk, 50000, 90, 0))
+    ce.ce_reg_write(c, cid, 1, enc_word(ce, sk, 7, 90, 16))
+    srv = ce.ce_server_create(c)
+    try:
+        t = ce.ce_server_submit(srv, cid, ce.insn("UDIV", 2, 0, 1))   # ~0.7 s on the GPU
+        with pytest.raises(ce.CeError) as ei:
+            ce.ce_client_evict(c, cid)
+        assert ei.value.code == -1
+        ce.ce_server_wait(srv, t, 600 * 10**9)
+    finally:
+        ce.ce_server_destroy(srv)
+    assert dec_word(ce, sk, ce.ce_reg_read(c, cid, 2)) == 50000 // 7
+    ce.ce_client_evict(c, cid)
+    with pytest.raises(ce.CeError) as ei:
+        ce.ce_reg_read(c, cid, 2)
+    assert ei.value.code == -6

@@ -158,3 +158,29 @@ def test_graph_replay_after_scratch_growth(ce, ctx, keys):
     bits = decrypt_all(ce, sk, d_out.cpu().numpy().view(np.uint32))
     for i in range(8):
         assert NL.from_bits(bits[i]) == int(a[i]) | int(b[i])
+
+
+def test_host_buffer_unit_call_equals_device_call(ce, ctx, keys):
+    """ce_unit_eval (host buffers in and out) returns exactly what
+    ce_unit_eval_device returns on the same inputs, at 16 and 32 bits."""
+    c, cid = ctx
+    sk, _ = keys
+    rng = np.random.default_rng(41)
+    a, b = operands(rng, 6)
+    inp = enc_operands(ce, sk, operand_bits(a, b), 13)
+    dev = run_unit(ce, ctx, "SUB", inp, W)
+    host = ce.ce_unit_eval(c, cid, "SUB", inp)
+    assert host.shape == dev.shape and (host == dev).all()
+    assert ce.ce_last_launch_count(c) > 0
+    bits = decrypt_all(ce, sk, host)
+    for i in range(6):
+        assert NL.from_bits(bits[i]) == (int(a[i]) - int(b[i])) & 0xFFFF
+    # width 32, AND: one level
+    w32 = np.stack([np.stack([ce.ce_encrypt_bit(sk, int(x), 14, 64 * i + j)
+                              for j, x in enumerate(rng.integers(0, 2, 64))]) for i in range(3)])
+    got = ce.ce_unit_eval(c, cid, "AND", w32, width=32)
+    import torch
+    d_out = torch.empty((3, 32, 501), dtype=torch.int32, device="cuda")
+    ce.ce_unit_eval_device_width(c, cid, "AND", 32, to_dev(w32.view(np.int32)), d_out, 3)
+    ce.ce_synchronize(c)
+    assert (got == d_out.cpu().numpy().view(np.uint32)).all()

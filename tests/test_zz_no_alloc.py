@@ -44,14 +44,17 @@ def test_noalloc_matches_allocating_entry_point(ce, ctx):
     ce.ce_gates_batch_device_noalloc(c, cid, d_ops, d_a, d_b, got, n, stream)
     ce.ce_synchronize(c)
     assert torch.equal(got, ref)
-    free_before, _ = torch.cuda.mem_get_info()
+    # the library counts its own device allocations and frees: none may
+    # happen inside the allocation-free calls (a balanced pair would too)
+    counts_before = ce.ce_device_alloc_count()
     for n, d_ops, d_a, d_b, ref, got in dev:      # two calls in a row
         got.zero_()
         ce.ce_gates_batch_device_noalloc(c, cid, d_ops, d_a, d_b, got, n, stream)
+        assert ce.ce_last_launch_count(c) == 3
         ce.ce_synchronize(c)
         assert torch.equal(got, ref), f"allocation-free output differs for n={n}"
-    free_after, _ = torch.cuda.mem_get_info()
-    assert free_after == free_before, "the allocation-free calls took device memory"
+    assert ce.ce_device_alloc_count() == counts_before, \
+        "the allocation-free calls allocated or freed device memory"
 
 
 def test_noalloc_rejects_oversized_batch(ce, ctx):

@@ -256,7 +256,8 @@ int ce_last_launch_count(ce_ctx *ctx);
 /* Functional units of the emulator (§5 "Data Processing Units", §6
  * "Conditional Flags") as netlists of bootstrapped gates.  Inputs: a[w]
  * then b[w] (bit 0 first); CSEL: rn[w], rm[w], N, Z, C, V.  Outputs: w bits;
- * CMP: N, Z, C, V of a - b; ADDS/SUBS: w bits then N, Z, C, V.  cond (CSEL only): 0 EQ, 1 NE, 2 CS, 3 CC, 4 MI,
+ * CMP: N, Z, C, V of a - b; ADDS/SUBS: w bits then N, Z, C, V; SMULL/UMULL:
+ * 2w bits.  cond (CSEL only): 0 EQ, 1 NE, 2 CS, 3 CC, 4 MI,
  * 5 PL, 6 VS, 7 VC, 8 HI, 9 LS, 10 GE, 11 LT, 12 GT, 13 LE. */
 typedef enum {
     CE_U_ADD = 0,         /* Kogge-Stone parallel-prefix adder (§5 "Adder") */
@@ -275,7 +276,12 @@ typedef enum {
     CE_U_EOR = 12,        /* bitwise XOR (§5 "Bitwise operations") */
     CE_U_ORN = 13,        /* bitwise a OR NOT b */
     CE_U_ADDS = 14,       /* a + b then its N, Z, C, V (outputs w + 4) */
-    CE_U_SUBS = 15        /* a - b then its N, Z, C, V (CMP keeping the difference) */
+    CE_U_SUBS = 15,       /* a - b then its N, Z, C, V (CMP keeping the difference) */
+    CE_U_SMULL = 16,      /* signed a * b, the full 2w-bit product, low half first
+                             (§5 "Signed multiplication": carry-save array, sign
+                             extension replaced by a constant; outputs 2w) */
+    CE_U_UMULL = 17       /* unsigned a * b, the full 2w-bit product (§5 "Unsigned
+                             multiplication", as an array; outputs 2w) */
 } ce_unit;
 
 /* Shape of a unit's netlist for width w (a power of two, 2..32). */
@@ -299,7 +305,7 @@ ce_status ce_unit_eval_device(ce_ctx *ctx, int client, int unit, int cond,
                               void *cuda_stream);
 /* The same at any width w (a power of two, 2..32; the paper's 32-bit units,
  * §5): d_in [n][2w (CSEL: 2w + 4)][501], d_out [n][w (CMP: 4)][501].
- * ce_unit_eval_device is this call with width 16.  CE_EINVAL for another
+ * (SMULL/UMULL: [n][2w][501]).  ce_unit_eval_device is this call with width 16.  CE_EINVAL for another
  * width. */
 ce_status ce_unit_eval_device_width(ce_ctx *ctx, int client, int unit, int cond, int width,
                                     const uint32_t *d_in, uint32_t *d_out, size_t n,
@@ -357,7 +363,15 @@ typedef enum {
     CE_I_REV = 25,     /* rd = rn with the two bytes swapped */
     CE_I_ADDS = 26,    /* rd = rn + rm, NZCV = its flags (§6 "Conditional Flags":
                           the flag-setting form) */
-    CE_I_SUBS = 27     /* rd = rn - rm, NZCV = flags(rn - rm) (§6, the SUBS example) */
+    CE_I_SUBS = 27,    /* rd = rn - rm, NZCV = flags(rn - rm) (§6, the SUBS example) */
+    CE_I_SMULH = 28,   /* rd = bits 16..31 of the signed product rn * rm (§5 "Signed
+                          multiplication"; the low half is CE_I_MUL's) */
+    CE_I_UMULH = 29,   /* rd = bits 16..31 of the unsigned product rn * rm */
+    /* Branches (§6 "Branch"): the program counter is cleartext; only
+     * ce_exec_branching runs them.  imm is the target instruction index
+     * (equal to the program length: end the program). */
+    CE_I_BCOND = 30,   /* if cond(NZCV) then pc = imm, decided by the key owner */
+    CE_I_B = 31        /* pc = imm */
 } ce_opcode;
 /* One cleartext instruction (§4 "Cloud service model": HE instructions are
  * unencrypted; §4 "Data Processing": register operands rd, rn, rm are vReg
@@ -378,9 +392,27 @@ ce_status ce_flags_read(ce_ctx *ctx, int client, ce_lwe nzcv[4]);
  * fetches cleartext instructions and runs them over encrypted vRegs; §6
  * "Branch and Control Flow" for the flags): blocking on the host until every
  * instruction is enqueued; results are read with ce_reg_read.  Malformed
- * instructions give CE_EINVAL; timeout_ns > 0 bounds the host time
- * (CE_ETIMEOUT). */
+ * instructions and branches (ce_exec_branching runs those) give CE_EINVAL;
+ * timeout_ns > 0 bounds the host time (CE_ETIMEOUT). */
 ce_status ce_exec(ce_ctx *ctx, int client, const ce_insn *prog, size_t n, uint64_t timeout_ns);
+/* Branch resolution by the key owner (§6 "Branch": the cloud sends the
+ * encrypted NZCV and the branch condition to a machine that owns the secret
+ * key, which decrypts them and returns the decision).  Called on the thread
+ * that runs ce_exec_branching, with no context lock held; nzcv (N first) is
+ * valid during the call.  Returns 1 (taken), 0 (not taken) or a negative
+ * value to abort the program. */
+typedef int (*ce_branch_fn)(void *user, int client, uint8_t cond, const ce_lwe *nzcv);
+/* Runs a program with branches (§6 "Branch and Control Flow": fetch at the
+ * cleartext PC, execute over encrypted vRegs, B.cond resolved through
+ * `decide`).  Straight-line runs between branches go through the engine as
+ * in ce_exec.  At most 256 instructions; max_steps > 0 bounds the executed
+ * instructions and timeout_ns > 0 the host time (CE_ETIMEOUT either way);
+ * *steps_out (may be NULL) receives the executed count.  CE_EINVAL for a
+ * target beyond the program end, a malformed instruction, or a negative
+ * decision. */
+ce_status ce_exec_branching(ce_ctx *ctx, int client, const ce_insn *prog, size_t n,
+                            ce_branch_fn decide, void *user, uint64_t max_steps,
+                            uint64_t timeout_ns, uint64_t *steps_out);
 /* Runs several programs concurrently (§5: independent work of the emulator
  * runs in parallel; here across programs and clients): their instructions
  * advance level by level together, so gates of different programs and

@@ -26,7 +26,7 @@ MUX = 10
 OPS = {"NAND": 0, "AND": 1, "OR": 2, "XOR": 3, "NOR": 4, "XNOR": 5, "ANDNY": 6, "ANDYN": 7,
        "ORNY": 8, "ORYN": 9}
 UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "CSEL", "LSR",
-         "ASR", "EOR", "ORN", "ADDS", "SUBS"]
+         "ASR", "EOR", "ORN", "ADDS", "SUBS", "SMULL", "UMULL"]
 CONDS = ["EQ", "NE", "CS", "CC", "MI", "PL", "VS", "VC", "HI", "LS", "GE", "LT", "GT", "LE"]
 
 
@@ -159,6 +159,51 @@ def cond_bit(net, cond, N, Z, C, V):
     return gt if name == "GT" else neg(gt)
 
 
+def full_product(net, a, b, signed):
+    """§5 "Signed multiplication" / "Unsigned multiplication": the whole
+    2w-bit product.  Signed operands: a * b = sum over i, j < w-1 of
+    a_j b_i 2^(i+j) + a_{w-1} b_{w-1} 2^(2w-2) - (sum over j < w-1 of
+    a_j b_{w-1} 2^(j+w-1) + the same with a, b swapped); each negative row
+    -x 2^k equals (NOT x - 1) 2^k, so the two rows become negated partial
+    products plus the constant -2 (2^(2w-2) - 2^(w-1)) = 2^w - 2^(2w-1), which
+    is 2^w + 2^(2w-1) mod 2^(2w): the constant that replaces the sign
+    extension.  2^w enters as the carry-in of the final adder and 2^(2w-1)
+    flips the top bit.  The partial products are summed row by row with
+    their carries kept (carry-save), then the high half by the prefix adder."""
+    w = len(a)
+    pp = []
+    for i in range(w):
+        row = []
+        for j in range(w):
+            x = net.g("AND", a[j], b[i])
+            row.append(neg(x) if signed and ((i == w - 1) != (j == w - 1)) else x)
+        pp.append(row)
+    S = {j: pp[0][j] for j in range(w)}
+    C = {}
+    for i in range(1, w):
+        nxt = {}
+        for k in range(i, i + w):
+            y = pp[i][k - i]
+            have = [v for v in (S.get(k), C.get(k)) if v is not None]
+            if not have:
+                S[k] = y
+            elif len(have) == 1:
+                x = have[0]
+                S[k] = net.g("XOR", x, y)
+                nxt[k + 1] = net.g("AND", x, y)
+            else:
+                x, c = S[k], C[k]
+                u = net.g("XOR", x, y)
+                S[k] = net.g("XOR", u, c)
+                nxt[k + 1] = net.mux(u, c, x)      # carry = majority(x, y, c)
+        C = nxt
+    # nothing reaches weight 2w-1 but the carry out of weights w..2w-2
+    hx = [S.get(w + k, FALSE) for k in range(w - 1)]
+    hy = [C.get(w + k, FALSE) for k in range(w - 1)]
+    hi, top = prefix_adder(net, hx, hy, "one" if signed else None)
+    return [S[k] for k in range(w)] + hi + [neg(top) if signed else top]
+
+
 def build(unit: str, w: int = 16, cond: int = 0) -> Net:
     net = Net(2 * w + (4 if unit == "CSEL" else 0))
     a = [net.inp(i) for i in range(w)]
@@ -248,6 +293,8 @@ def build(unit: str, w: int = 16, cond: int = 0) -> Net:
         y2 = net.g("ANDYN", y1, s[w - 1])
         V = net.g("OR", x2, y2)
         out = s + [N, Z, carry, V]
+    elif unit in ("SMULL", "UMULL"):
+        out = full_product(net, a, b, unit == "SMULL")
     elif unit == "CSEL":
         N, Z, C, V = (net.inp(2 * w + i) for i in range(4))
         c = cond_bit(net, cond, N, Z, C, V)
@@ -313,6 +360,12 @@ def armv8(unit: str, a: int, b: int, w: int = 16, cond: int = 0, nzcv: int = 0):
         return (sa >> (b % w)) & m
     if unit == "MUL":
         return (a * b) & m
+    if unit == "UMULL":
+        return a * b
+    if unit == "SMULL":
+        sa = a - (1 << w) if a >> (w - 1) else a
+        sb = b - (1 << w) if b >> (w - 1) else b
+        return (sa * sb) & ((1 << 2 * w) - 1)
     if unit == "UDIV":
         return 0 if b == 0 else a // b
     if unit == "CMP":
@@ -353,6 +406,10 @@ def armv8_insn(op: str, rd: int, rn: int, rm: int, imm: int, cond: int, nzcv: in
         return rn, nzcv
     if op == "MOV_IMM":
         return imm, nzcv
+    if op == "SMULH":
+        return armv8("SMULL", rn, rm, w) >> w, nzcv
+    if op == "UMULH":
+        return armv8("UMULL", rn, rm, w) >> w, nzcv
     if op in ("LSL_IMM", "LSR_IMM", "ASR_IMM"):
         return armv8(op[:3], rn, imm % w, w), nzcv
     if op == "MVN":

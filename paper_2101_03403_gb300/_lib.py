@@ -85,6 +85,7 @@ def lib() -> ctypes.CDLL:
         "ce_flags_read": (i32, [vp, i32, vp]),
         "ce_exec": (i32, [vp, i32, vp, sz, u64]),
         "ce_exec_multi": (i32, [vp, sz, vp, vp, vp, u64]),
+        "ce_exec_branching": (i32, [vp, i32, vp, sz, vp, vp, u64, u64, ctypes.POINTER(u64)]),
         "ce_server_create": (i32, [vp, i32, pp]),
         "ce_server_submit": (i32, [vp, i32, vp, ctypes.POINTER(u64)]),
         "ce_server_poll": (i32, [vp, u64, ctypes.POINTER(i32), ctypes.POINTER(u64),
@@ -376,7 +377,7 @@ def ce_profile_read(ctx: Context) -> dict:
 
 
 UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "CSEL", "LSR",
-         "ASR", "EOR", "ORN", "ADDS", "SUBS"]
+         "ASR", "EOR", "ORN", "ADDS", "SUBS", "SMULL", "UMULL"]
 UNIT_ID = {u: i for i, u in enumerate(UNITS)}
 
 
@@ -416,7 +417,8 @@ def ce_unit_netlist(unit, cond: int = 0, width: int = 16) -> dict:
 
 OPCODES = ["ADD", "SUB", "AND", "ORR", "LSL", "LSL_IMM", "MUL", "UDIV", "CMP", "CSEL", "MOV",
            "MOV_IMM", "LSR", "ASR", "LSR_IMM", "ASR_IMM", "EOR", "ORN", "MVN", "AND_IMM", "ORR_IMM",
-           "EOR_IMM", "BFC", "BFI", "RBIT", "REV", "ADDS", "SUBS"]
+           "EOR_IMM", "BFC", "BFI", "RBIT", "REV", "ADDS", "SUBS", "SMULH", "UMULH", "BCOND",
+           "B"]
 OPCODE_ID = {o: i for i, o in enumerate(OPCODES)}
 CONDS = ["EQ", "NE", "CS", "CC", "MI", "PL", "VS", "VC", "HI", "LS", "GE", "LT", "GT", "LE"]
 
@@ -495,6 +497,35 @@ def ce_exec_multi(ctx: Context, clients, progs, timeout_ns: int = 0):
     ptrs = (ctypes.c_void_p * len(progs))(*[ctypes.addressof(a) for a, _ in arrs])
     lens = (ctypes.c_size_t * len(progs))(*[n for _, n in arrs])
     _check(lib().ce_exec_multi(ctx.ptr, len(progs), cl, ptrs, lens, timeout_ns), "ce_exec_multi")
+
+
+BRANCH_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint8,
+                             ctypes.c_void_p)
+
+
+def ce_exec_branching(ctx: Context, client: int, prog, decide, max_steps: int = 0,
+                      timeout_ns: int = 0) -> int:
+    """Run a program with branches; decide(client, cond, nzcv[4][501]) -> bool
+    is the key owner's branch decision.  Returns the executed step count."""
+    arr, n = _prog(prog)
+    err = []
+
+    def cb(_user, client_, cond, p):
+        try:
+            nz = np.ctypeslib.as_array((ctypes.c_uint32 * (4 * LWE_WORDS)).from_address(p))
+            return 1 if decide(client_, int(cond), nz.reshape(4, LWE_WORDS).copy()) else 0
+        except Exception as e:            # surfaced after the call
+            err.append(e)
+            return -1
+
+    fn = BRANCH_FN(cb)
+    steps = ctypes.c_uint64()
+    code = lib().ce_exec_branching(ctx.ptr, client, ctypes.addressof(arr), n, fn, None, max_steps,
+                                   timeout_ns, ctypes.byref(steps))
+    if err:
+        raise err[0]
+    _check(code, "ce_exec_branching")
+    return steps.value
 
 
 class Server:

@@ -750,7 +750,8 @@ enum Opcode : uint8_t {
   kAdd = 0, kSub = 1, kAnd = 2, kOrr = 3, kLsl = 4, kLslImm = 5, kMul = 6, kUdiv = 7,
   kCmp = 8, kCsel = 9, kMov = 10, kMovImm = 11, kLsr = 12, kAsr = 13, kLsrImm = 14,
   kAsrImm = 15, kEor = 16, kOrn = 17, kMvn = 18, kAndImm = 19, kOrrImm = 20, kEorImm = 21,
-  kBfc = 22, kBfi = 23, kRbit = 24, kRev = 25, kAdds = 26, kSubs = 27, kOpcodes = 28
+  kBfc = 22, kBfi = 23, kRbit = 24, kRev = 25, kAdds = 26, kSubs = 27, kSmulh = 28,
+  kUmulh = 29, kBcond = 30, kB = 31, kOpcodes = 32
 };
 
 // Instructions that only move, negate or fix wires (no bootstrap, §5 "Data
@@ -797,6 +798,8 @@ int unit_of(uint8_t op) {
     case kOrn: return kUnitOrn;
     case kAdds: return kUnitAdds;
     case kSubs: return kUnitSubs;
+    case kSmulh: return kUnitSmull;
+    case kUmulh: return kUnitUmull;
     default: return -1;
   }
 }
@@ -820,6 +823,9 @@ ce_status advance(Engine &E, Run &r) {
     const ce_insn &I = r.code[r.pc];
     if (I.op >= kOpcodes || I.rd >= kRegs || I.rn >= kRegs || I.rm >= kRegs || I.cond > 13)
       return set_error(CE_EINVAL, "ce_exec: malformed instruction at index " + std::to_string(r.pc));
+    if (I.op == kBcond || I.op == kB)
+      return set_error(CE_EINVAL, "ce_exec: branch at index " + std::to_string(r.pc) +
+                                      " (programs with branches run through ce_exec_branching)");
     SRef probe;
     if (wire_move(I, R.r[I.rd], R.r[I.rn], 0, &probe)) {
       SRef nv[kWidth];
@@ -850,13 +856,15 @@ void retire(Engine &E, Run &r) {
   const ce_insn &I = r.code[r.pc];
   E.complete(*r.cur);
   RegFile &R = E.regs(r.client);
-  // CMP: result = NZCV; ADDS/SUBS: rd bits then NZCV; others: rd bits
+  // CMP: result = NZCV; ADDS/SUBS: rd bits then NZCV; SMULH/UMULH: the
+  // high half of the 32-bit product; others: rd bits
   const bool flags = I.op == kCmp || I.op == kAdds || I.op == kSubs;
   const int first_flag = I.op == kCmp ? 0 : kWidth;
+  const int first_bit = (I.op == kSmulh || I.op == kUmulh) ? kWidth : 0;
   if (I.op != kCmp)
     for (int j = 0; j < kWidth; ++j) {
       E.unref(R.r[I.rd][j]);
-      R.r[I.rd][j] = r.cur->result[j];
+      R.r[I.rd][j] = r.cur->result[first_bit + j];
     }
   if (flags)
     for (int k = 0; k < 4; ++k) {
@@ -1221,5 +1229,65 @@ extern "C" ce_status ce_trace_read(ce_ctx *ctx, ce_trace_rec *out, size_t cap, s
   if (e != cudaSuccess) return cuda_error(e, "ce_trace_read");
   *count = n;
   if (seen) *seen = total;
+  return CE_OK;
+}
+
+extern "C" ce_status ce_exec_branching(ce_ctx *ctx, int client, const ce_insn *prog, size_t n,
+                                       ce_branch_fn decide, void *user, uint64_t max_steps,
+                                       uint64_t timeout_ns, uint64_t *steps_out) {
+  if (steps_out) *steps_out = 0;
+  if (!ctx || (n && !prog) || !decide)
+    return set_error(CE_EINVAL, "ce_exec_branching: bad argument");
+  if (n > 256) return set_error(CE_EINVAL, "ce_exec_branching: at most 256 instructions");
+  for (size_t i = 0; i < n; ++i)
+    if ((prog[i].op == kB || prog[i].op == kBcond) && prog[i].imm > n)
+      return set_error(CE_EINVAL, "ce_exec_branching: branch target beyond the program end");
+  const auto t0 = std::chrono::steady_clock::now();
+  auto left_ns = [&]() -> uint64_t {
+    if (!timeout_ns) return 0;
+    const uint64_t dt = uint64_t(std::chrono::duration_cast<std::chrono::nanoseconds>(
+                                     std::chrono::steady_clock::now() - t0)
+                                     .count());
+    return dt >= timeout_ns ? 1 : timeout_ns - dt;
+  };
+  uint64_t steps = 0;
+  size_t pc = 0;
+  while (pc < n) {
+    // straight-line run up to the next branch: one program of the engine
+    size_t end = pc;
+    while (end < n && prog[end].op != kB && prog[end].op != kBcond) ++end;
+    if (max_steps && steps + (end - pc) > max_steps)
+      return set_error(CE_ETIMEOUT, "ce_exec_branching: step limit reached");
+    if (end > pc) {
+      const ce_insn *seg = prog + pc;
+      const size_t len = end - pc;
+      int ticks = 0;
+      ce_status s = exec_programs(ctx, 1, &client, &seg, &len, left_ns(), ctx->stream, &ticks);
+      if (s != CE_OK) return s;
+      steps += len;
+      pc = end;
+      if (steps_out) *steps_out = steps;
+    }
+    if (pc == n) break;
+    if (max_steps && steps + 1 > max_steps)
+      return set_error(CE_ETIMEOUT, "ce_exec_branching: step limit reached");
+    const ce_insn &I = prog[pc];
+    bool taken = true;
+    if (I.op == kBcond) {
+      if (I.cond > 13) return set_error(CE_EINVAL, "ce_exec_branching: bad condition");
+      // the cloud hands the encrypted flags and the condition to the key
+      // owner, who returns the decision; no context lock is held meanwhile
+      ce_lwe nzcv[4];
+      ce_status s = ce_flags_read(ctx, client, nzcv);
+      if (s != CE_OK) return s;
+      const int d = decide(user, client, I.cond, nzcv);
+      if (d < 0) return set_error(CE_EINVAL, "ce_exec_branching: the branch decision failed");
+      taken = d != 0;
+    }
+    pc = taken ? size_t(I.imm) : pc + 1;
+    ++steps;
+    if (steps_out) *steps_out = steps;
+    if (timeout_ns && left_ns() == 1) return set_error(CE_ETIMEOUT, "ce_exec_branching: timeout");
+  }
   return CE_OK;
 }

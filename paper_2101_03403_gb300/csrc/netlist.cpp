@@ -168,6 +168,73 @@ Ref condition(Builder &B, int cond, Ref N, Ref Z, Ref C, Ref V) {
   }
 }
 
+// Full-width array multiplier: the 2w-bit product of a and b.  Partial
+// products pp[i][j] = a_j AND b_i at weight i + j.  Signed (§5 "Signed
+// multiplication": the partial products' sign extension to 2w bits replaced
+// by a constant, the Baugh-Wooley form): the bits with exactly one of i, j
+// equal to w - 1 enter negated (a free NOT of the AND), and 2^w + 2^(2w-1) is
+// added, 2^w as the carry-in of the final adder and 2^(2w-1) as a negation of
+// the product's top bit.  Rows 1..w-1 add pp[i] into the running sum at
+// weights i..i+w-1 together with the previous row's carries (carry-save: a
+// full adder is s = x ^ y ^ c, carry = (x ^ y) ? c : x as one MUX; a cell
+// with two inputs is a half adder, with one a wire); bit k < w is final after
+// row k, and the high half is the Kogge-Stone sum of the remaining sum and
+// carry bits (§5 "Adder").
+std::vector<Ref> full_multiplier(Builder &B, const std::vector<Ref> &a, const std::vector<Ref> &b,
+                                 bool sign) {
+  const int w = static_cast<int>(a.size());
+  std::vector<std::vector<Ref>> pp(w, std::vector<Ref>(w));
+  for (int i = 0; i < w; ++i)
+    for (int j = 0; j < w; ++j) {
+      pp[i][j] = B.gate(AND, a[j], b[i]);
+      if (sign && ((i == w - 1) != (j == w - 1))) pp[i][j] = !pp[i][j];
+    }
+  std::vector<Ref> S(2 * w), C(2 * w + 1);
+  std::vector<bool> hasS(2 * w, false), hasC(2 * w + 1, false);
+  for (int j = 0; j < w; ++j) {
+    S[j] = pp[0][j];
+    hasS[j] = true;
+  }
+  for (int i = 1; i < w; ++i) {
+    std::vector<Ref> nC(2 * w + 1);
+    std::vector<bool> nhas(2 * w + 1, false);
+    for (int k = i; k < i + w; ++k) {
+      const Ref y = pp[i][k - i];
+      if (!hasS[k] && !hasC[k]) {
+        S[k] = y;
+      } else if (!hasS[k] || !hasC[k]) {
+        const Ref x = hasS[k] ? S[k] : C[k];
+        S[k] = B.gate(XOR, x, y);
+        nC[k + 1] = B.gate(AND, x, y);
+        nhas[k + 1] = true;
+      } else {
+        const Ref x = S[k];
+        const Ref u = B.gate(XOR, x, y);
+        S[k] = B.gate(XOR, u, C[k]);
+        nC[k + 1] = B.mux(u, C[k], x);
+        nhas[k + 1] = true;
+      }
+      hasS[k] = true;
+    }
+    C = nC;
+    hasC = nhas;
+  }
+  // Weight 2w-1 holds no sum or carry bit (the top cell of every row only
+  // passes its partial product on), so the high half is the (w-1)-bit sum of
+  // weights w..2w-2 with its carry-out as bit 2w-1.
+  std::vector<Ref> hx(w - 1), hy(w - 1);
+  for (int k = 0; k + 1 < w; ++k) {
+    hx[k] = hasS[w + k] ? S[w + k] : constant(false);
+    hy[k] = hasC[w + k] ? C[w + k] : constant(false);
+  }
+  AdderOut r = kogge_stone(B, hx, hy, sign ? 1 : 0, Ref{});
+  std::vector<Ref> hi = r.sum;
+  hi.push_back(sign ? !r.carry : r.carry);
+  std::vector<Ref> o(S.begin(), S.begin() + w);
+  o.insert(o.end(), hi.begin(), hi.end());
+  return o;
+}
+
 }  // namespace
 
 int32_t Netlist::bootstraps() const {
@@ -322,6 +389,10 @@ bool build_unit(int unit, int w, int cond, Netlist *out) {
       o.push_back(V);
       break;
     }
+    case kUnitSmull:
+    case kUnitUmull:
+      o = full_multiplier(B, a, b, unit == kUnitSmull);
+      break;
     case kUnitCsel: {
       const Ref N = B.in(2 * w), Z = B.in(2 * w + 1), C = B.in(2 * w + 2), V = B.in(2 * w + 3);
       const Ref c = condition(B, cond, N, Z, C, V);

@@ -61,12 +61,15 @@ enum Unit : int {
   kUnitOrn = 13,       // bitwise a OR NOT b
   kUnitAdds = 14,      // a + b and its NZCV (flag-setting add, §6)
   kUnitSubs = 15,      // a - b and its NZCV (CMP that keeps the difference)
-  kUnitCount = 16
+  kUnitSmull = 16,     // signed a * b, full 2w-bit product (§5 "Signed multiplication")
+  kUnitUmull = 17,     // unsigned a * b, full 2w-bit product (§5 "Unsigned multiplication")
+  kUnitCount = 18
 };
 
 // Inputs: a[width] then b[width] (CSEL: rn[width], rm[width], N, Z, C, V).
 // Outputs: width bits (CMP: N, Z, C, V; ADDS/SUBS: width bits then N, Z, C,
-// V).  Returns false for a bad request.
+// V; SMULL/UMULL: 2 width bits, low half first).  Returns false for a bad
+// request.
 bool build_unit(int unit, int width, int cond, Netlist *out);
 
 }  // namespace ce

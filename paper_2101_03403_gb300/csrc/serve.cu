@@ -68,6 +68,7 @@ struct ce_server {
   std::deque<uint64_t> queue;             // submitted, not started
   std::map<int, uint64_t> running;        // client -> ticket in flight
   std::deque<std::pair<cudaEvent_t, std::vector<uint64_t>>> pending;  // retired, awaiting GPU
+  std::deque<cudaEvent_t> ticks_in_flight;  // one event per enqueued tick, oldest first
   std::vector<cudaEvent_t> ev_free;
   uint64_t next_ticket = 1;
   bool stop = false;
@@ -152,6 +153,14 @@ void serve_loop(ce_server *s) {
       return !s->running.empty();
     }();
     if (work) {
+      // At most two ticks in flight on the GPU: wait for older ones here,
+      // outside the context lock, so that other calls on the context get
+      // their turn between ticks instead of waiting for the whole queue.
+      while (s->ticks_in_flight.size() >= 2) {
+        cudaEventSynchronize(s->ticks_in_flight.front());
+        s->ev_free.push_back(s->ticks_in_flight.front());
+        s->ticks_in_flight.pop_front();
+      }
       ce_status st = engine_serve_tick(s->ctx, s->stream, start_clients, start_insns, retired,
                                        &active, &boots);
       if (st != CE_OK) {
@@ -167,6 +176,9 @@ void serve_loop(ce_server *s) {
       }
       ++s->ticks;
       s->bootstraps += uint64_t(boots);
+      cudaEvent_t te = take_ev(s);
+      cudaEventRecord(te, s->stream);
+      s->ticks_in_flight.push_back(te);
       if (!retired.empty()) {
         std::vector<uint64_t> ids;
         {
@@ -225,7 +237,7 @@ extern "C" ce_status ce_server_create(ce_ctx *ctx, int max_inflight, ce_server *
 extern "C" ce_status ce_server_submit(ce_server *s, int client, const ce_insn *insn,
                                       uint64_t *ticket) {
   if (!s || !insn || !ticket) return set_error(CE_EINVAL, "ce_server_submit: bad argument");
-  if (insn->op > CE_I_SUBS || insn->rd > 7 || insn->rn > 7 || insn->rm > 7 || insn->cond > 13)
+  if (insn->op > CE_I_UMULH || insn->rd > 7 || insn->rn > 7 || insn->rm > 7 || insn->cond > 13)
     return set_error(CE_EINVAL, "ce_server_submit: malformed instruction");
   // the client stays admitted while its ticket is queued: eviction checks
   // the queue under the same lock
@@ -300,6 +312,8 @@ extern "C" void ce_server_destroy(ce_server *s) {
   if (s->worker.joinable()) s->worker.join();
   reap(s, true);
   cudaStreamSynchronize(s->stream);
+  for (auto e : s->ticks_in_flight) s->ev_free.push_back(e);
+  s->ticks_in_flight.clear();
   {
     std::lock_guard<std::recursive_mutex> lock(s->ctx->mu);
     auto &v = s->ctx->servers;

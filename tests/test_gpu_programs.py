@@ -76,7 +76,8 @@ def test_every_instruction(ce, ctx, keys):
     c, cid = ctx
     sk, _ = keys
     rng = np.random.default_rng(2022)
-    ops = [o for o in ce.OPCODES if o not in ("MUL", "UDIV")]   # those two: test below
+    # MUL, UDIV: test below; branches: ce_exec_branching (test below)
+    ops = [o for o in ce.OPCODES if o not in ("MUL", "UDIV", "BCOND", "B")]
     prog = [("CMP", 0, 1, 2, 0, 0)]
     for op in rng.permutation(ops + ops):
         prog.append((str(op), int(rng.integers(8)), int(rng.integers(8)), int(rng.integers(8)),
@@ -112,3 +113,66 @@ def test_program_errors(ce, ctx):
         ce.ce_exec(c, cid, [ce.insn("ADD", 0, 1, 2)] * 4, timeout_ns=1)
     assert ei.value.code == -4
     ce.ce_synchronize(c)
+
+
+def run_plain_branching(prog, regs, max_steps=10000):
+    """The plaintext machine with a cleartext program counter (§6 "Branch")."""
+    regs, nzcv, pc, steps = list(regs), 0, 0, 0
+    while pc < len(prog):
+        op, rd, rn, rm, imm, cond = prog[pc]
+        steps += 1
+        assert steps <= max_steps
+        if op == "B":
+            pc = imm
+        elif op == "BCOND":
+            pc = imm if NL.armv8("CSEL", 1, 0, W, cond, nzcv) else pc + 1
+        else:
+            regs[rd], nzcv = NL.armv8_insn(op, regs[rd], regs[rn], regs[rm], imm, cond, nzcv, W)
+            pc += 1
+    return regs, nzcv, steps
+
+
+def test_branching_loop_resolved_by_the_key_owner(ce, ctx, keys):
+    """A counted loop closed by B.NE, an unconditional branch over dead code,
+    and the signed/unsigned high-half multiplies; the branch decisions are
+    made by a callback that decrypts the encrypted NZCV with the secret key
+    (the client side of §6's branch resolution)."""
+    c, cid = ctx
+    sk, _ = keys
+    prog = [("MOV_IMM", 3, 0, 0, 1, 0), ("MOV_IMM", 4, 0, 0, 0, 0), ("MOV_IMM", 2, 0, 0, 0, 0),
+            ("ADD", 2, 2, 0, 0, 0),            # 3: loop body
+            ("SUB", 1, 1, 3, 0, 0),
+            ("CMP", 0, 1, 4, 0, 0),
+            ("BCOND", 0, 0, 0, 3, 1),          # B.NE 3
+            ("SMULH", 5, 2, 0, 0, 0),
+            ("B", 0, 0, 0, 10, 0),
+            ("MOV_IMM", 6, 0, 0, 77, 0),       # skipped
+            ("UMULH", 7, 0, 2, 0, 0)]
+    init = [0xC123, 3, 0, 0, 0, 0, 0x5555, 0]
+    load_regs(ce, c, cid, sk, init, 44)
+    asked = []
+
+    def decide(client, cond, nzcv):
+        f = [ce.ce_decrypt_bit(sk, x) for x in nzcv]
+        asked.append((client, cond))
+        return NL.armv8("CSEL", 1, 0, W, cond, f[0] | f[1] << 1 | f[2] << 2 | f[3] << 3) == 1
+
+    steps = ce.ce_exec_branching(c, cid, [ce.insn(*i) for i in prog], decide, max_steps=100)
+    exp_regs, exp_nzcv, exp_steps = run_plain_branching(prog, init)
+    assert steps == exp_steps
+    assert asked == [(cid, 1)] * 3                      # three B.NE decisions
+    assert read_regs(ce, c, cid, sk) == exp_regs
+    assert exp_regs[6] == 0x5555                          # the dead code stayed dead
+
+
+def test_branching_errors(ce, ctx):
+    c, cid = ctx
+    with pytest.raises(ce.CeError) as ei:                   # ce_exec runs no branches
+        ce.ce_exec(c, cid, [ce.insn("B", imm=1)])
+    assert ei.value.code == -1
+    with pytest.raises(ce.CeError) as ei:                   # an endless loop hits the step limit
+        ce.ce_exec_branching(c, cid, [ce.insn("B", imm=0)], lambda *a: True, max_steps=50)
+    assert ei.value.code == -4
+    with pytest.raises(ce.CeError) as ei:                   # target beyond the end
+        ce.ce_exec_branching(c, cid, [ce.insn("B", imm=5)], lambda *a: True)
+    assert ei.value.code == -1

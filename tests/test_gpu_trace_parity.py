@@ -165,3 +165,28 @@ def test_serving_mix_levels_match_oracle(ce, ctx, keys, O, full_keys):
         ce.ce_trace_enable(c, 0)
         for e in extra:
             ce.ce_client_evict(c, e)
+
+
+def test_signed_multiplier_levels_match_oracle(ce, ctx, keys, O, full_keys):
+    """16-bit SMULL (the full 32-bit signed product, §5 "Signed
+    multiplication"): two sampled gates of every level against the oracle,
+    and the decrypted product against signed semantics."""
+    import torch
+    c, cid = ctx
+    sk, _ = keys
+    a, b = 0x8003, 0x7FF1                      # negative times positive
+    bits = [(a >> j) & 1 for j in range(W)] + [(b >> j) & 1 for j in range(W)]
+    inp = np.stack([ce.ce_encrypt_bit(sk, x, 47, j) for j, x in enumerate(bits)])[None]
+    d_out = torch.empty((1, 2 * W, 501), dtype=torch.int32, device="cuda")
+    ce.ce_trace_enable(c, 2, 4096)
+    try:
+        ce.ce_unit_eval_device(c, cid, "SMULL", to_dev(inp.view(np.int32)), d_out, 1, 0)
+        ce.ce_synchronize(c)
+        recs, _ = ce.ce_trace_read(c)
+    finally:
+        ce.ce_trace_enable(c, 0)
+    depth = ce.ce_unit_info("SMULL")["depth"]
+    assert sorted(set(recs["tick"].tolist())) == list(range(depth))
+    assert oracle_check(O, {cid: full_keys}, recs) == []
+    out = d_out.cpu().numpy().view(np.uint32)[0]
+    assert NL.from_bits([ce.ce_decrypt_bit(sk, x) for x in out]) == NL.armv8("SMULL", a, b, W)

@@ -56,13 +56,13 @@ def operands(rng, n):
 
 
 @pytest.mark.parametrize("unit", ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "CMP",
-                                  "LSR", "ASR", "EOR", "ORN", "ADDS", "SUBS"])
+                                  "LSR", "ASR", "EOR", "ORN", "ADDS", "SUBS", "SMULL", "UMULL"])
 def test_unit_semantics(ce, ctx, keys, unit):
     sk, _ = keys
     rng = np.random.default_rng(sum(map(ord, unit)))
     n = 40
     a, b = operands(rng, n)
-    n_out = {"CMP": 4, "ADDS": W + 4, "SUBS": W + 4}.get(unit, W)
+    n_out = {"CMP": 4, "ADDS": W + 4, "SUBS": W + 4, "SMULL": 2 * W, "UMULL": 2 * W}.get(unit, W)
     out = run_unit(ce, ctx, unit, enc_operands(ce, sk, operand_bits(a, b), 5), n_out)
     bits = decrypt_all(ce, sk, out)
     for i in range(n):

@@ -62,3 +62,19 @@ def test_register_instructions_and_flags():
         assert (N, Z, C) == (r >> 15, int(r == 0), int(rn >= rm))
         sa, sb = rn - (rn >> 15 << 16), rm - (rm >> 15 << 16)
         assert V == int(not -32768 <= sa - sb <= 32767)
+
+
+def test_high_half_multiplies():
+    """SMULH / UMULH: the high 16 bits of the 32-bit product, against the
+    product of the operands read as signed (two's complement) or unsigned
+    integers, including the corner cases of the signed range."""
+    rng = np.random.default_rng(10)
+    pairs = [(int(a), int(b)) for a, b in rng.integers(0, 1 << 16, (300, 2))]
+    pairs += [(0x8000, 0x8000), (0x8000, 0x7FFF), (0xFFFF, 0xFFFF), (0xFFFF, 1), (0, 0x8000)]
+    for rn, rm in pairs:
+        sa = rn - 65536 if rn >= 32768 else rn
+        sb = rm - 65536 if rm >= 32768 else rm
+        p = sa * sb
+        assert NL.armv8_insn("SMULH", 0, rn, rm, 0, 0, 0)[0] == (p // 65536) % 65536
+        assert NL.armv8_insn("UMULH", 0, rn, rm, 0, 0, 0)[0] == (rn * rm) // 65536
+        assert NL.armv8("SMULL", rn, rm, 16) == p % (1 << 32)

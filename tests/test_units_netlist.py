@@ -8,7 +8,7 @@ import pytest
 from oracle import netlists as NL
 
 UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "LSR", "ASR",
-         "EOR", "ORN", "ADDS", "SUBS"]
+         "EOR", "ORN", "ADDS", "SUBS", "SMULL", "UMULL"]
 
 
 def eval_vec(net, inputs):
@@ -46,6 +46,11 @@ def check_unit(unit, w, a, b, cond=0, nzcv=None):
         assert (got == exp[:, 0]).all(), unit
         for k in range(4):
             assert (outs[w + k] == exp[:, 1 + k]).all(), (unit, k)
+    elif unit in ("SMULL", "UMULL"):           # 2w-bit products (Python integers)
+        got = [sum(int(outs[i][k]) << i for i in range(2 * w)) for k in range(len(a))]
+        exp = [NL.armv8(unit, int(x), int(y), w) for x, y in zip(a, b)]
+        bad = [k for k in range(len(a)) if got[k] != exp[k]]
+        assert not bad, (unit, int(a[bad[0]]), int(b[bad[0]]), got[bad[0]], exp[bad[0]])
     else:
         got = sum(outs[i].astype(np.int64) << i for i in range(w))
         if unit == "CSEL":
@@ -163,6 +168,15 @@ def test_structure_matches_the_paper():
     sub = NL.build("SUB", 16)
     # §6: Z by a 15-OR tree, V by 5 gates
     assert len(cmp_.gates) == len(sub.gates) + 15 + 5
+    # §5 "Signed multiplication": all w^2 partial products at level 1, of
+    # which exactly 2(w-1) enter negated (the rows the sign extension made
+    # negative), and a full 2w-bit product
+    for unit, negated in (("SMULL", 30), ("UMULL", 0)):
+        m = NL.build(unit, 16)
+        pp = [g[4] for g in m.gates if g[5] == 1]
+        assert len(pp) == 256 and len(m.outputs) == 32
+        uses = [r for g in m.gates for r in (g[1], g[2], g[3]) if r[0] in set(pp)]
+        assert len({r[0] for r in uses if r[1]}) == negated, unit
 
 
 @pytest.fixture(scope="module")

@@ -42,8 +42,9 @@ void dev_free(void *p) {
   g_dev_frees.fetch_add(1, std::memory_order_relaxed);
 }
 
-// Per-thread twist factors of the two-prime transform (rns_ntt.cuh) with
-// their Shoup quotients; the inverse table carries the 1/1024 scale.
+// Per-thread factors of the two-prime transform (rns_ntt.cuh) with their
+// Shoup quotients: twists (the inverse ones carry the 1/1024 scale) and the
+// middle-phase twiddles.
 void transform_tables(uint4 *out) {
   const uint32_t ps[2] = {rns::P<0>(), rns::P<1>()};
   const uint32_t roots[2] = {rns::Psi<0>(), rns::Psi<1>()};
@@ -56,6 +57,16 @@ void transform_tables(uint4 *out) {
         const uint32_t wf = rns::powm(psi, e, p);
         const uint32_t wi = rns::mulm(rns::powm(psi_inv, e, p), inv1024, p);
         uint4 &F = out[k2 * 64 + n1], &I = out[1024 + k2 * 64 + n1];
+        (q == 0 ? F.x : F.z) = wf;
+        (q == 0 ? F.y : F.w) = rns::shoup_of(wf, p);
+        (q == 0 ? I.x : I.z) = wi;
+        (q == 0 ? I.y : I.w) = rns::shoup_of(wi, p);
+      }
+    for (int a = 0; a < 8; ++a)
+      for (int c = 0; c < 8; ++c) {
+        const uint64_t e = uint64_t(32) * a * c;
+        const uint32_t wf = rns::powm(psi, e, p), wi = rns::powm(psi_inv, e, p);
+        uint4 &F = out[2048 + a * 8 + c], &I = out[2112 + a * 8 + c];
         (q == 0 ? F.x : F.z) = wf;
         (q == 0 ? F.y : F.w) = rns::shoup_of(wf, p);
         (q == 0 ? I.x : I.z) = wi;

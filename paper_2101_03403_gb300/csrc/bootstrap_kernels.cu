@@ -15,6 +15,8 @@
 #include "launch.h"
 #include "rns_ntt.cuh"
 
+static_assert(ce::kTwistEntries == size_t(rns::kTwEntries), "factor table size");
+
 namespace ce {
 
 namespace {
@@ -154,7 +156,6 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::kRing + G * L::kGate);
   uint32_t *count = reinterpret_cast<uint32_t *>(full + NSLOT);
   volatile int *abort = reinterpret_cast<volatile int *>(count + NSLOT);
-  const uint4 *tw_fwd = tw, *tw_inv = tw + 1024;
   constexpr int kChunksPerGate = kLweN * kGadgetL;  // 1500
   constexpr int kWarps = 4 * G;
 
@@ -241,19 +242,25 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
           v[0][n2] = rns::pretwist<0>(u + (rns::P<0>() - 512u), n2);
           v[1][n2] = rns::pretwist<1>(u + (rns::P<1>() - 512u), n2);
         }
-        rns::forward(v, Y, buf, t, 1 + g, 128, tw_fwd);
+        rns::forward(v, Y, buf, t, 1 + g, 128, tw);
         wait_slot(smem_u32(full + slot), uint32_t(chunk / NSLOT) & 1u, abort, err);
         // X[o] += Y[0] * key(c=0, p, o) + Y[1] * key(c=1, p, o), per prime;
-        // key words are (k mod p0, k mod p1) in Montgomery form.
-        const uint2 *key = reinterpret_cast<const uint2 *>(ring) + size_t(slot) * kChunkWords + t;
+        // key words are (k mod p0, k mod p1) in Montgomery form, positions d
+        // and d+1 in one 16-byte word.
+        const uint4 *key = reinterpret_cast<const uint4 *>(ring + size_t(slot) * kChunkWords) + t;
 #pragma unroll
-        for (int d = 0; d < 8; ++d) {
+        for (int dp = 0; dp < 4; ++dp) {
 #pragma unroll
           for (int o = 0; o < 2; ++o) {
-            const uint2 k0 = key[((0 * 2 + o) * 8 + d) * 128];
-            const uint2 k1 = key[((1 * 2 + o) * 8 + d) * 128];
+            const uint4 k0 = key[((0 * 2 + o) * 4 + dp) * 128];
+            const uint4 k1 = key[((1 * 2 + o) * 4 + dp) * 128];
+            const int d = 2 * dp;
             X[0][o][d] += rns::redc<0>(uint64_t(Y[0][0][d]) * k0.x + uint64_t(Y[0][1][d]) * k1.x);
             X[1][o][d] += rns::redc<1>(uint64_t(Y[1][0][d]) * k0.y + uint64_t(Y[1][1][d]) * k1.y);
+            X[0][o][d + 1] +=
+                rns::redc<0>(uint64_t(Y[0][0][d + 1]) * k0.z + uint64_t(Y[0][1][d + 1]) * k1.z);
+            X[1][o][d + 1] +=
+                rns::redc<1>(uint64_t(Y[1][0][d + 1]) * k0.w + uint64_t(Y[1][1][d + 1]) * k1.w);
           }
         }
         // Release the slot; the last warp out refills it with chunk + NSLOT.
@@ -272,16 +279,9 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
         }
       }
       {
-        // Three levels of [0, 2p) terms: below 6p; the inverse takes [0, 4p).
-#pragma unroll
-        for (int o = 0; o < 2; ++o)
-#pragma unroll
-          for (int d = 0; d < 8; ++d) {
-            X[0][o][d] = rns::fold<0, 4>(X[0][o][d]);
-            X[1][o][d] = rns::fold<1, 4>(X[1][o][d]);
-          }
+        // three levels of terms below 3p: below 9p, which the inverse takes
         uint32_t v[2][16];
-        rns::inverse(X, v, buf, t, 1 + g, 128, tw_inv);
+        rns::inverse(X, v, buf, t, 1 + g, 128, tw);
         uint32_t *dst = acc + P * kRingN + n1;
 #pragma unroll
         for (int n2 = 0; n2 < 16; ++n2) dst[64 * n2] += rns::lift32(v[0][n2], v[1][n2]);
@@ -327,7 +327,6 @@ __global__ void __launch_bounds__(384, 1) blind_rotate_wide_kernel(
   const int g = threadIdx.x >> 7, t = threadIdx.x & 127;
   uint2 *buf = bufs + g * rns::kBufWords;
   uint64_t *slot = slots + size_t(g) * kChunkWords;
-  const uint4 *tw_fwd = tw, *tw_inv = tw + 1024;
   const int my_gates = int(blockIdx.x) < n_jobs ? (n_jobs - 1 - int(blockIdx.x)) / int(gridDim.x) + 1 : 0;
   const int total = my_gates * kLweN;  // chunks per group
   auto chunk_src = [&](int c) {
@@ -378,19 +377,24 @@ __global__ void __launch_bounds__(384, 1) blind_rotate_wide_kernel(
           v[1][n2] = rns::pretwist<1>(u + (rns::P<1>() - 512u), n2);
         }
       }
-      rns::forward(v, Y, buf, t, 1 + g, 128, tw_fwd);
+      rns::forward(v, Y, buf, t, 1 + g, 128, tw);
       wait_slot(smem_u32(full + g), uint32_t(c) & 1u, abort, err);
-      uint32_t X[2][2][8];  // this level's products, each in [0, 2p)
+      uint32_t X[2][2][8];  // this level's products, each below 3p
       {
-        const uint2 *key = reinterpret_cast<const uint2 *>(slot) + t;
+        const uint4 *key = reinterpret_cast<const uint4 *>(slot) + t;
 #pragma unroll
-        for (int d = 0; d < 8; ++d)
+        for (int dp = 0; dp < 4; ++dp)
 #pragma unroll
           for (int o = 0; o < 2; ++o) {
-            const uint2 k0 = key[((0 * 2 + o) * 8 + d) * 128];
-            const uint2 k1 = key[((1 * 2 + o) * 8 + d) * 128];
+            const uint4 k0 = key[((0 * 2 + o) * 4 + dp) * 128];
+            const uint4 k1 = key[((1 * 2 + o) * 4 + dp) * 128];
+            const int d = 2 * dp;
             X[0][o][d] = rns::redc<0>(uint64_t(Y[0][0][d]) * k0.x + uint64_t(Y[0][1][d]) * k1.x);
             X[1][o][d] = rns::redc<1>(uint64_t(Y[1][0][d]) * k0.y + uint64_t(Y[1][1][d]) * k1.y);
+            X[0][o][d + 1] =
+                rns::redc<0>(uint64_t(Y[0][0][d + 1]) * k0.z + uint64_t(Y[0][1][d + 1]) * k1.z);
+            X[1][o][d + 1] =
+                rns::redc<1>(uint64_t(Y[1][0][d + 1]) * k0.w + uint64_t(Y[1][1][d + 1]) * k1.w);
           }
       }
       rns::named_bar(1 + g, 128);  // the group is done with its slot
@@ -409,12 +413,12 @@ __global__ void __launch_bounds__(384, 1) blind_rotate_wide_kernel(
         for (int o = 0; o < 2; ++o)
 #pragma unroll
           for (int d = 0; d < 8; ++d) {
-            // three [0, 2p) terms: below 6p; the inverse takes [0, 4p)
+            // three terms below 3p: below 9p, which the inverse takes
             const uint2 a1 = x1[(o * 8 + d) * 128], a2 = x2[(o * 8 + d) * 128];
-            X[0][o][d] = rns::fold<0, 4>(X[0][o][d] + a1.x + a2.x);
-            X[1][o][d] = rns::fold<1, 4>(X[1][o][d] + a1.y + a2.y);
+            X[0][o][d] = X[0][o][d] + a1.x + a2.x;
+            X[1][o][d] = X[1][o][d] + a1.y + a2.y;
           }
-        rns::inverse(X, v, buf, t, 1, 128, tw_inv);
+        rns::inverse(X, v, buf, t, 1, 128, tw);
         uint32_t *dst = acc + P * kRingN + n1;
 #pragma unroll
         for (int n2 = 0; n2 < 16; ++n2) dst[64 * n2] += rns::lift32(v[0][n2], v[1][n2]);
@@ -535,8 +539,9 @@ __global__ void zero_slots_kernel(const GateOut *__restrict__ outs, uint32_t *__
 // Block (i, p): transforms the four polynomials (TRGSW half c, component o)
 // of bootstrapping-key rows r = c*3 + p of key bit i (coefficients lifted to
 // [-2^31, 2^31)) and stores them, reduced and in Montgomery form, in the
-// [i][p][c*2+o][d][thread] order the blind rotation reads: one 64-bit word
-// per position holding the residues (mod p0, mod p1).
+// [i][p][c*2+o][d/2][thread][d%2] order the blind rotation reads (one
+// 16-byte load gives a thread its positions d and d+1): one 64-bit word per
+// position holding the residues (mod p0, mod p1).
 __global__ void __launch_bounds__(128) bsk_to_transform_kernel(const uint32_t *__restrict__ bsk,
                                                                uint2 *__restrict__ out,
                                                                const uint4 *__restrict__ tw) {
@@ -558,7 +563,7 @@ __global__ void __launch_bounds__(128) bsk_to_transform_kernel(const uint32_t *_
     for (int o = 0; o < 2; ++o)
 #pragma unroll
       for (int d = 0; d < 8; ++d)
-        dst[((c * 2 + o) * 8 + d) * 128 + t] =
+        dst[((c * 2 + o) * 4 + d / 2) * 256 + 2 * t + (d & 1)] =
             make_uint2(rns::fold<0, 1>(rns::to_mont<0>(X[0][o][d])),
                        rns::fold<1, 1>(rns::to_mont<1>(X[1][o][d])));
   }
@@ -589,7 +594,8 @@ __global__ void __launch_bounds__(128) negacyclic_mul_kernel(const int16_t *__re
     v[1][n2] = rns::pretwist<1>(rns::from_i32<1>(x), n2);
   }
   rns::forward(v, XK, buf, t, 1, 128, tw);
-  // XD * XK = redc(XD * mont(XK)); mont(XK) < 2p keeps the product below 2^59.
+  // XD * XK = redc(XD * mont(XK)): XD < 16p and mont(XK) < 2p keep the
+  // product below 32 p^2 < 2^61 and the reduction below 3p.
 #pragma unroll
   for (int q = 0; q < 2; ++q)
 #pragma unroll
@@ -597,7 +603,7 @@ __global__ void __launch_bounds__(128) negacyclic_mul_kernel(const int16_t *__re
       XD[0][q][d] = rns::redc<0>(uint64_t(XD[0][q][d]) * rns::to_mont<0>(XK[0][q][d]));
       XD[1][q][d] = rns::redc<1>(uint64_t(XD[1][q][d]) * rns::to_mont<1>(XK[1][q][d]));
     }
-  rns::inverse(XD, v, buf, t, 1, 128, tw + 1024);
+  rns::inverse(XD, v, buf, t, 1, 128, tw);
   if (live) {
 #pragma unroll
     for (int n2 = 0; n2 < 16; ++n2)

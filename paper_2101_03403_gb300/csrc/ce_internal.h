@@ -31,8 +31,9 @@ constexpr int kSlotWords = 512;       // engine arena slot: a[500], b, padding
 // Key-switching key on the device keeps only v = 1..3 (v = 0 adds nothing):
 // [j][q][v-1][kKskRow] uint32.
 constexpr uint64_t kKskDevWords = uint64_t(kRingN) * kKsT * 3 * kKskRow;
-// Bootstrapping key in the transform domain: [i][p][4][8][128] uint64 with
-// 4 = (TRGSW half c, output component o) and [8][128] = (register d, thread).
+// Bootstrapping key in the transform domain: [i][p][4][4][128][2] uint64
+// with 4 = (TRGSW half c, output component o) and [4][128][2] = (register
+// pair d/2, thread, d%2).
 constexpr int kChunkWords = 4 * 8 * 128;                  // 4096 uint64 = 32 KB
 constexpr uint64_t kBskNttWords = uint64_t(kLweN) * kGadgetL * kChunkWords;
 

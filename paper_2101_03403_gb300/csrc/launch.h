@@ -88,11 +88,13 @@ struct GatePathResources {
   cudaStream_t stream;
 };
 
-// Twist tables of the two-prime transform, one uint4 {w0, w0', w1, w1'} per
-// entry (residue mod p_q and its Shoup quotient): forward psi_q^((2 k2 + 1) n1)
-// at [k2 * 64 + n1], inverse psi_q^(-(2 k2 + 1) n1) / 1024 at
-// [1024 + k2 * 64 + n1].
-constexpr size_t kTwistEntries = 2048;
+// Factor table of the two-prime transform, one uint4 {w0, w0', w1, w1'} per
+// entry (residue mod p_q and its Shoup quotient): forward twist
+// psi_q^((2 k2 + 1) n1) at [k2 * 64 + n1], inverse twist
+// psi_q^(-(2 k2 + 1) n1) / 1024 at [1024 + k2 * 64 + n1], middle-phase
+// twiddles psi_q^(32 a c) at [2048 + a * 8 + c] and psi_q^(-32 a c) at
+// [2112 + a * 8 + c].
+constexpr size_t kTwistEntries = 2176;
 void transform_tables(uint4 *host_out /* kTwistEntries */);
 
 }  // namespace ce

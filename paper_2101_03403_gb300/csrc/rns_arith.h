@@ -86,6 +86,14 @@ constexpr uint32_t kCrt = invm(0x0FFF0001u % 0x0FFEF801u, 0x0FFEF801u);
 constexpr uint32_t kCrtP = shoup_of(kCrt, 0x0FFEF801u);
 static_assert(kPP > (uint64_t(6 * 1024) << 41), "P exceeds twice the largest |exact sum|");
 
+// Per-thread factor table (global memory, L1-resident), entries uint4
+// {w mod p0, its Shoup quotient, w mod p1, its Shoup quotient}:
+//   [0, 1024)      forward twist psi^(n1 (2 k2 + 1)) at k2 * 64 + n1,
+//   [1024, 2048)   inverse twist psi^(-n1 (2 k2 + 1)) / 1024,
+//   [2048, 2112)   forward middle-phase twiddle psi^(32 a c) at a * 8 + c,
+//   [2112, 2176)   inverse middle-phase twiddle psi^(-32 a c).
+constexpr int kTwInv = 1024, kTwC1Fwd = 2048, kTwC1Inv = 2112, kTwEntries = 2176;
+
 struct Tw {
   uint32_t w, wp;
 };
@@ -96,7 +104,6 @@ struct Uniform {
   Tw pre[2][2][16];  // [dir][q][n2]: psi^(+-64 n2)
   Tw r16[2][2][8];   // [dir][q][e]: psi^(+-128 e)
   Tw r8[2][2][4];    // [dir][q][e]: psi^(+-256 e)
-  Tw c1[2][2][64];   // [dir][q][a * 8 + c]: psi^(+-32 a c)
 };
 
 constexpr Uniform make_uniform() {
@@ -120,11 +127,6 @@ constexpr Uniform make_uniform() {
         const uint32_t w = powm(r, 256u * e, p);
         u.r8[dir][q][e] = Tw{w, shoup_of(w, p)};
       }
-      for (int a = 0; a < 8; ++a)
-        for (int c = 0; c < 8; ++c) {
-          const uint32_t w = powm(r, 32u * a * c, p);
-          u.c1[dir][q][a * 8 + c] = Tw{w, shoup_of(w, p)};
-        }
     }
   }
   return u;

@@ -24,7 +24,7 @@ using namespace rns;
 static const uint32_t kPr[2] = {P<0>(), P<1>()};
 
 static void tables(std::vector<uint4> &tw) {
-  tw.assign(2048, uint4{});
+  tw.assign(kTwEntries, uint4{});
   const uint32_t roots[2] = {Psi<0>(), Psi<1>()};
   for (int q = 0; q < 2; ++q) {
     const uint32_t p = kPr[q], psi = roots[q], pinv = invm(psi, p), n_inv = invm(1024, p);
@@ -33,6 +33,15 @@ static void tables(std::vector<uint4> &tw) {
         const uint64_t e = uint64_t(2 * k2 + 1) * n1;
         const uint32_t wf = powm(psi, e, p), wi = mulm(powm(pinv, e, p), n_inv, p);
         uint4 &F = tw[k2 * 64 + n1], &I = tw[1024 + k2 * 64 + n1];
+        (q ? F.z : F.x) = wf;
+        (q ? F.w : F.y) = shoup_of(wf, p);
+        (q ? I.z : I.x) = wi;
+        (q ? I.w : I.y) = shoup_of(wi, p);
+      }
+    for (int a = 0; a < 8; ++a)
+      for (int c = 0; c < 8; ++c) {
+        const uint32_t wf = powm(psi, 32u * a * c, p), wi = powm(pinv, 32u * a * c, p);
+        uint4 &F = tw[kTwC1Fwd + a * 8 + c], &I = tw[kTwC1Inv + a * 8 + c];
         (q ? F.z : F.x) = wf;
         (q ? F.w : F.y) = shoup_of(wf, p);
         (q ? I.z : I.x) = wi;
@@ -56,7 +65,7 @@ static void forward2(const std::vector<uint4> &tw, const uint32_t (*in)[2][1024]
     }
     fwd_phase_a(v, buf.data(), t, tw.data());
   }
-  for (int t = 0; t < 128; ++t) fwd_phase_c1(buf.data(), t >> 5, t & 31);
+  for (int t = 0; t < 128; ++t) fwd_phase_c1(buf.data(), t >> 5, t & 31, tw.data() + kTwC1Fwd);
   for (int t = 0; t < 128; ++t) fwd_phase_c2(X[t], buf.data(), t);
 }
 
@@ -125,18 +134,16 @@ int main() {
   for (int t = 0; t < 128; ++t)
     for (int o = 0; o < 2; ++o)
       for (int d = 0; d < 8; ++d) {
-        rns_range_check(X[t][0][o][d] < 6 * kPr[0] && X[t][1][o][d] < 6 * kPr[1]);
-        X[t][0][o][d] = fold<0, 4>(X[t][0][o][d]);
-        X[t][1][o][d] = fold<1, 4>(X[t][1][o][d]);
+        rns_range_check(X[t][0][o][d] < kInvIn * kPr[0] && X[t][1][o][d] < kInvIn * kPr[1]);
       }
   std::vector<uint2> buf(kBufWords);
   for (int t = 0; t < 128; ++t) inv_phase_c2(X[t], buf.data(), t);
-  for (int t = 0; t < 128; ++t) inv_phase_c1(buf.data(), t >> 5, t & 31);
+  for (int t = 0; t < 128; ++t) inv_phase_c1(buf.data(), t >> 5, t & 31, tw.data() + kTwC1Inv);
   static uint32_t out[2][1024];
   for (int t = 0; t < 128; ++t) {
     const int Pp = t >> 6, n1 = t & 63;
     uint32_t v[2][16];
-    inv_phase_a(v, buf.data(), t, tw.data() + 1024);
+    inv_phase_a(v, buf.data(), t, tw.data() + kTwInv);
     for (int n2 = 0; n2 < 16; ++n2) out[Pp][n1 + 64 * n2] = lift32(v[0][n2], v[1][n2]);
   }
   fwrite(out, sizeof out, 1, stdout);

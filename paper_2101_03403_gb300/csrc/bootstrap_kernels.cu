@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
       // all zero, so the step adds exactly zero.
       const int rot = active ? __ldg(ab + i) : 0;
       uint32_t w[16];
-      uint32_t X[2][2][8];  // [prime][output polynomial][position]
+      uint64_t XL[2][2][8];  // [prime][output polynomial][position], unreduced key sums
       {
         // w = X^rot ACC_P - ACC_P + decomposition offset, at n = n1 + 64 n2.
         const uint32_t *src = acc + P * kRingN;
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
 #pragma unroll
           for (int o = 0; o < 2; ++o)
 #pragma unroll
-            for (int d = 0; d < 8; ++d) X[q][o][d] = 0;
+            for (int d = 0; d < 8; ++d) XL[q][o][d] = 0;
       }
 #pragma unroll 1
       for (int pz = 0; pz < kGadgetL; ++pz, ++chunk) {
@@ -255,12 +255,10 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
             const uint4 k0 = key[((0 * 2 + o) * 4 + dp) * 128];
             const uint4 k1 = key[((1 * 2 + o) * 4 + dp) * 128];
             const int d = 2 * dp;
-            X[0][o][d] += rns::redc<0>(uint64_t(Y[0][0][d]) * k0.x + uint64_t(Y[0][1][d]) * k1.x);
-            X[1][o][d] += rns::redc<1>(uint64_t(Y[1][0][d]) * k0.y + uint64_t(Y[1][1][d]) * k1.y);
-            X[0][o][d + 1] +=
-                rns::redc<0>(uint64_t(Y[0][0][d + 1]) * k0.z + uint64_t(Y[0][1][d + 1]) * k1.z);
-            X[1][o][d + 1] +=
-                rns::redc<1>(uint64_t(Y[1][0][d + 1]) * k0.w + uint64_t(Y[1][1][d + 1]) * k1.w);
+            XL[0][o][d] += uint64_t(Y[0][0][d]) * k0.x + uint64_t(Y[0][1][d]) * k1.x;
+            XL[1][o][d] += uint64_t(Y[1][0][d]) * k0.y + uint64_t(Y[1][1][d]) * k1.y;
+            XL[0][o][d + 1] += uint64_t(Y[0][0][d + 1]) * k0.z + uint64_t(Y[0][1][d + 1]) * k1.z;
+            XL[1][o][d + 1] += uint64_t(Y[1][0][d + 1]) * k0.w + uint64_t(Y[1][1][d + 1]) * k1.w;
           }
         }
         // Release the slot; the last warp out refills it with chunk + NSLOT.
@@ -279,8 +277,17 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
         }
       }
       {
-        // three levels of terms below 3p: below 9p, which the inverse takes
-        uint32_t v[2][16];
+        // six products of a value below 16p and a key below p: below 96 p^2
+        // < 2^63; one Montgomery reduction gives below 96 p^2 / 2^32 + p < 7p,
+        // which the inverse takes
+        uint32_t X[2][2][8], v[2][16];
+#pragma unroll
+        for (int o = 0; o < 2; ++o)
+#pragma unroll
+          for (int d = 0; d < 8; ++d) {
+            X[0][o][d] = rns::redc<0>(XL[0][o][d]);
+            X[1][o][d] = rns::redc<1>(XL[1][o][d]);
+          }
         rns::inverse(X, v, buf, t, 1 + g, 128, tw);
         uint32_t *dst = acc + P * kRingN + n1;
 #pragma unroll

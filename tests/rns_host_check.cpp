@@ -113,7 +113,10 @@ int main() {
           }
     }
 
-  // One CMux step's external product, accumulated as the kernel does.
+  // One CMux step's external product, accumulated as the kernel does: the
+  // six key products of an output position summed unreduced in 64 bits,
+  // then one Montgomery reduction.
+  static uint64_t XL[128][2][2][8];
   static uint32_t X[128][2][2][8];
   for (int l = 0; l < 3; ++l) {
     static uint32_t din[2][2][1024];
@@ -125,16 +128,18 @@ int main() {
     for (int t = 0; t < 128; ++t)
       for (int o = 0; o < 2; ++o)
         for (int d = 0; d < 8; ++d) {
-          X[t][0][o][d] += redc<0>(uint64_t(Y[t][0][0][d]) * KX[l][0][t][0][o][d] +
-                                   uint64_t(Y[t][0][1][d]) * KX[l][1][t][0][o][d]);
-          X[t][1][o][d] += redc<1>(uint64_t(Y[t][1][0][d]) * KX[l][0][t][1][o][d] +
-                                   uint64_t(Y[t][1][1][d]) * KX[l][1][t][1][o][d]);
+          XL[t][0][o][d] += uint64_t(Y[t][0][0][d]) * KX[l][0][t][0][o][d] +
+                            uint64_t(Y[t][0][1][d]) * KX[l][1][t][0][o][d];
+          XL[t][1][o][d] += uint64_t(Y[t][1][0][d]) * KX[l][0][t][1][o][d] +
+                            uint64_t(Y[t][1][1][d]) * KX[l][1][t][1][o][d];
         }
   }
   for (int t = 0; t < 128; ++t)
     for (int o = 0; o < 2; ++o)
       for (int d = 0; d < 8; ++d) {
-        rns_range_check(X[t][0][o][d] < kInvIn * kPr[0] && X[t][1][o][d] < kInvIn * kPr[1]);
+        X[t][0][o][d] = redc<0>(XL[t][0][o][d]);
+        X[t][1][o][d] = redc<1>(XL[t][1][o][d]);
+        rns_range_check(X[t][0][o][d] < 7 * kPr[0] && X[t][1][o][d] < 7 * kPr[1]);
       }
   std::vector<uint2> buf(kBufWords);
   for (int t = 0; t < 128; ++t) inv_phase_c2(X[t], buf.data(), t);

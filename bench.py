@@ -393,7 +393,17 @@ def run_ours(args, rank: int, world: int, local: int):
     peak_tops = int_peak_tops(sms, sm_mhz)
     forms = external_product_forms(ce, ctx, cid, stream, dev, rng, d_min, d_mout, mul_n,
                                    peak_tops) if rank == 0 else None
-    serving = serving_leg(ce, ctx) if rank == 0 else None
+    programs = serving = None
+    if rank == 0:
+        from paper_2101_03403_gb300 import serve_bench
+        extra, _, _ = serve_bench.admit_clients(ce, ctx, 32, SEED + 1000, rng)
+        programs = programs_leg(ce, ctx, extra, rng)
+        for k, (cid, sk) in enumerate(extra[:16]):    # serving reads r0, r1, r3 (r3 nonzero)
+            ce.ce_reg_write(ctx, cid, 3, np.stack(
+                [ce.ce_encrypt_bit(sk, ((k + 1) >> j) & 1, 950 + k, j) for j in range(16)]))
+        serving = serving_leg(ce, ctx, extra[:16])
+        for cid, _ in extra:
+            ce.ce_client_evict(ctx, cid)
 
     br_ms, br_launches = prof["blind_rotate"]
     achieved = boots * args.steps * OPS_PER_GATE / (br_ms / 1e3) / 1e12
@@ -440,6 +450,7 @@ def run_ours(args, rank: int, world: int, local: int):
                                "mul16_batch64_p50": pct(mul_ms, 50),
                                "mul16_bootstraps": mul_boots},
                 "serving": serving,
+                "programs": programs,
                 "e2e": {"value": e2e_val, "unit": UNIT,
                         "h2d_bytes_per_step": int(host_in.nbytes),
                         "d2h_bytes_per_step": int(n * 16 * 501 * 4)},
@@ -449,12 +460,76 @@ def run_ours(args, rank: int, world: int, local: int):
     ctx.close()
 
 
-def serving_leg(ce, ctx, clients: int = 16, requests: int = 256, load: float = 0.9):
+def program_set(rng, n=32, lo=8, hi=64):
+    """Register programs of seeded random length lo..hi over 8 registers:
+    ADD, SUB, AND, ORR, LSL (register and immediate), CMP, and conditional-
+    select loops (a cleartext trip count of 2..4 of CMP; CSEL)."""
+    progs = []
+    for _ in range(n):
+        length = int(rng.integers(lo, hi + 1))
+        prog = [("CMP", 0, 1, 2, 0, 0)]                  # flags defined before any CSEL
+        while len(prog) < length:
+            kind = str(rng.choice(["ADD", "SUB", "AND", "ORR", "LSL", "LSL_IMM", "CMP",
+                                   "CSEL_LOOP"]))
+            r = [int(x) for x in rng.integers(0, 8, 3)]
+            if kind == "CSEL_LOOP":
+                cond = int(rng.integers(14))
+                for _ in range(int(rng.integers(2, 5))):
+                    prog += [("CMP", 0, r[1], r[2], 0, 0), ("CSEL", r[0], r[1], r[2], 0, cond)]
+            elif kind == "LSL_IMM":
+                prog.append(("LSL_IMM", r[0], r[1], 0, int(rng.integers(16)), 0))
+            else:
+                prog.append((kind, r[0], r[1], r[2], 0, 0))
+        progs.append(prog[:length])
+    return progs
+
+
+def programs_leg(ce, ctx, clients, rng):
+    """32 register programs, one per client, advancing together: the eager
+    tick loop against the planned program set replayed as a captured CUDA
+    graph (identical ciphertexts checked), wall time with a device sync."""
+    progs = program_set(rng, len(clients))
+    init = [[int(x) for x in rng.integers(0, 1 << 16, 8)] for _ in clients]
+    ids = [cid for cid, _ in clients]
+    code = [[ce.insn(*i) for i in p] for p in progs]
+
+    def load():
+        for k, (cid, sk) in enumerate(clients):
+            for r, v in enumerate(init[k]):
+                ce.ce_reg_write(ctx, cid, r, np.stack(
+                    [ce.ce_encrypt_bit(sk, (v >> j) & 1, 900 + k, 16 * r + j) for j in range(16)]))
+
+    def run(graphs):
+        load()
+        ce.ce_set_unit_graphs(ctx, graphs)
+        ce.ce_synchronize(ctx)
+        t0 = time.perf_counter()
+        ce.ce_exec_multi(ctx, ids, code)
+        ce.ce_synchronize(ctx)
+        ms = (time.perf_counter() - t0) * 1e3
+        regs = [ce.ce_reg_read(ctx, cid, r) for cid in ids[:4] for r in range(8)]
+        return ms, regs
+
+    eager_ms, eager = run(False)
+    first_ms, _ = run(True)                       # plans the set and captures its graph
+    replay_ms, replay = run(True)
+    ce.ce_set_unit_graphs(ctx, True)
+    assert all((a == b).all() for a, b in zip(eager, replay)), "program graph replay differs"
+    n_ins = sum(len(p) for p in progs)
+    return {"programs": len(progs), "instructions": n_ins,
+            "lengths_min_max": [min(map(len, progs)), max(map(len, progs))],
+            "eager_ms": eager_ms, "graph_plan_and_first_run_ms": first_ms,
+            "graph_replay_ms": replay_ms, "per_program_ms_eager": eager_ms / len(progs),
+            "per_program_ms_graph": replay_ms / len(progs), "identical_outputs": True}
+
+
+def serving_leg(ce, ctx, clients, requests: int = 256, load: float = 0.9):
     """Short serving run (the configs' request mix at Poisson arrivals, a
     fraction of the measured saturated rate): per-request p50/p99 latency and
-    bootstraps/s.  Clients get their own seeded key sets."""
+    bootstraps/s.  Clients have their own seeded key sets."""
     from paper_2101_03403_gb300 import serve_bench
-    res = serve_bench.serve(ce, ctx, clients, requests, [load], seed=SEED + 1000)
+    res = serve_bench.serve(ce, ctx, len(clients), requests, [load], seed=SEED + 1000,
+                            clients=clients)
     pt = res["points"][0]
     return {"clients": res["clients_admitted"], "requests": pt["requests"], "load": load,
             "mix": res["mix"], "requests_per_s": pt["requests_per_s"],

@@ -318,7 +318,13 @@ ce_status ce_unit_eval_device_width(ce_ctx *ctx, int client, int unit, int cond,
  * CE_EINVAL for a device-side failure of this call's work. */
 ce_status ce_unit_eval(ce_ctx *ctx, int client, int unit, int cond, int width,
                        const ce_lwe *in, ce_lwe *out, size_t n);
-/* Graph replay of ce_unit_eval_device on (1, default) or off (eager). */
+/* Graph replay (1, default) or eager launches (0) for ce_unit_eval_device,
+ * ce_unit_eval and register programs (ce_exec, ce_exec_multi): with graphs
+ * on, a program set is planned on its first run (every tick recorded on the
+ * host against slots the plan owns) and replayed as one captured CUDA graph,
+ * the clients' registers copied in and out; results are bit-identical to
+ * the eager tick loop.  Program calls with a host time limit (timeout_ns >
+ * 0) always run the eager tick loop. */
 ce_status ce_set_unit_graphs(ce_ctx *ctx, int on);
 
 /* ------------------------------------------- encrypted register programs --- */

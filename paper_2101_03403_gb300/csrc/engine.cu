@@ -105,6 +105,17 @@ __global__ void trace_kernel(const GateJob *__restrict__ jobs, const GateOut *__
   }
 }
 
+// arena[dst] = (neg ? -1 : 1) * arena[src] for the (src, neg, dst) triples
+// of map (register bits copied into and out of a program plan's slots).
+__global__ void copy_slots_kernel(const uint32_t *__restrict__ map, uint32_t *__restrict__ arena) {
+  const size_t c = blockIdx.x;
+  const uint32_t src = map[3 * c], neg = map[3 * c + 1], dst = map[3 * c + 2];
+  for (int m = threadIdx.x; m < kLweWords; m += blockDim.x) {
+    const uint32_t v = arena[size_t(src) * kSlotWords + m];
+    arena[size_t(dst) * kSlotWords + m] = neg ? 0u - v : v;
+  }
+}
+
 __global__ void fill_false_kernel(uint32_t *__restrict__ arena) {
   for (int m = threadIdx.x; m < kSlotWords; m += blockDim.x)
     arena[m] = (m == kLweN) ? 0u - kMuEighth : 0u;
@@ -139,7 +150,7 @@ struct RegFile {
 };
 
 struct Plan {
-  int unit = 0, cond = 0, width = 0, client = 0, xp = 0;
+  int unit = 0, cond = 0, width = 0, client = 0, xp = 0, ks = 0;
   size_t n = 0;
   const uint32_t *d_in = nullptr;
   uint32_t *d_out = nullptr;
@@ -162,11 +173,38 @@ struct Plan {
   uint64_t last_use = 0;
 };
 
+// A set of register programs (cleartext, no branches) planned once: every
+// tick's descriptors recorded against slots the plan owns, then captured as
+// one CUDA graph.  A run copies the clients' current register bits into the
+// plan's input slots, replays the ticks, and copies the final register bits
+// into fresh slots of the register files (copy maps uploaded per run).
+constexpr int kRegBits = kRegs * kWidth + 4;  // 8 x 16 register bits + NZCV
+struct ProgPlan {
+  int xp = 0, ks = 0;                       // external-product form, key-switch engine
+  std::vector<int> clients;                 // per program
+  std::vector<std::vector<uint8_t>> code;   // per program: instruction bytes
+  std::vector<int> regfiles;                // distinct clients, in first-use order
+  uint32_t in_base = 0;                     // kRegBits input slots per register file
+  std::vector<uint32_t> slots;              // slots the plan owns (one reference each)
+  std::vector<Plan::Level> levels;
+  size_t max_jobs = 0;
+  uint8_t *d_desc = nullptr;
+  std::vector<std::vector<SRef>> final_refs;  // per register file: kRegBits refs
+  size_t n_out_copies = 0;                  // final refs that are not constants
+  uint32_t *d_map = nullptr;                // copy-in triples, then copy-out triples
+  cudaGraphExec_t exec = nullptr;
+  uint64_t exec_gen = 0;
+  int graph_launches = 0;
+  uint64_t last_use = 0;
+  int ticks = 0;
+};
+
 class Engine {
  public:
   explicit Engine(ce_ctx *c) : ctx(c) {}
   ~Engine() {
     for (auto &p : plans) drop_plan(*p);
+    for (auto &p : pplans) drop_prog_plan(*p);
     for (int i = 0; i < 2; ++i) {
       if (h_desc[i]) cudaFreeHost(h_desc[i]);
       dev_free(d_desc[i]);
@@ -209,6 +247,7 @@ class Engine {
       dev_free(arena);
       // plans captured the old address
       for (auto &p : plans) drop_graph(*p);
+      for (auto &p : pplans) drop_prog_graph(*p);
     }
     arena = na;
     cap = ncap;
@@ -262,6 +301,15 @@ class Engine {
       if ((*pit)->client == client) {
         drop_plan(**pit);
         pit = plans.erase(pit);
+      } else {
+        ++pit;
+      }
+    }
+    for (auto pit = pplans.begin(); pit != pplans.end();) {
+      const auto &cl = (*pit)->regfiles;
+      if (std::find(cl.begin(), cl.end(), client) != cl.end()) {
+        drop_prog_plan(**pit);
+        pit = pplans.erase(pit);
       } else {
         ++pit;
       }
@@ -502,12 +550,73 @@ class Engine {
     for (uint32_t sl : p.slots) unref(SRef{sl, false});
     p.slots.clear();
   }
+  void drop_prog_graph(ProgPlan &p) {
+    if (p.exec) cudaGraphExecDestroy(p.exec);
+    p.exec = nullptr;
+  }
+  void drop_prog_plan(ProgPlan &p) {
+    drop_prog_graph(p);
+    dev_free(p.d_desc);
+    dev_free(p.d_map);
+    p.d_desc = nullptr;
+    p.d_map = nullptr;
+    for (auto &refs : p.final_refs)
+      for (const SRef &r : refs) unref(r);
+    p.final_refs.clear();
+    for (uint32_t sl : p.slots) unref(SRef{sl, false});
+    p.slots.clear();
+  }
+  // Appends a built tick's descriptors to a plan blob; the plan takes a
+  // reference on every slot the tick writes, so no later work reuses it.
+  Plan::Level record_level(const TickDesc &t, std::vector<uint8_t> &blob,
+                           std::vector<uint32_t> &owned) {
+    auto put = [&](const void *src, size_t bytes) {
+      const size_t off = align16(blob.size());
+      blob.resize(off + bytes);
+      if (bytes) std::memcpy(blob.data() + off, src, bytes);
+      return off;
+    };
+    Plan::Level lv{};
+    lv.n_jobs = int(t.jobs.size());
+    lv.n_outs = int(t.outs.size());
+    lv.G = t.G;
+    lv.blocks = t.blocks;
+    lv.tile = t.tile;
+    lv.jsplit = t.jsplit;
+    lv.ks_planes = t.ks_planes;
+    lv.br_hankel = t.br_hankel;
+    lv.jobs_off = put(t.jobs.data(), t.jobs.size() * sizeof(GateJob));
+    lv.outs_off = put(t.outs.data(), t.outs.size() * sizeof(GateOut));
+    lv.bsk_off = put(t.grp_bsk.data(), t.grp_bsk.size() * sizeof(void *));
+    lv.ksk_off = put(t.tile_ksk.data(), t.tile_ksk.size() * sizeof(void *));
+    for (const GateOut &o : t.outs)
+      if (o.slot > kSlotSink) {
+        ref(SRef{o.slot, false});
+        owned.push_back(o.slot);
+      }
+    return lv;
+  }
+  // Launches recorded levels whose descriptors live at d_desc.
+  ce_status launch_levels(const std::vector<Plan::Level> &levels, const uint8_t *d_desc,
+                          cudaStream_t st, int *launches) {
+    for (const Plan::Level &lv : levels) {
+      ce_status s = launch_level(reinterpret_cast<const GateJob *>(d_desc + lv.jobs_off), lv.n_jobs,
+                                 reinterpret_cast<const GateOut *>(d_desc + lv.outs_off), lv.n_outs,
+                                 reinterpret_cast<const uint64_t *const *>(d_desc + lv.bsk_off),
+                                 reinterpret_cast<const uint32_t *const *>(d_desc + lv.ksk_off),
+                                 lv.G, lv.blocks, lv.tile, lv.jsplit, lv.ks_planes, lv.br_hankel, st,
+                                 launches);
+      if (s != CE_OK) return s;
+    }
+    return CE_OK;
+  }
 
   ce_status make_plan(int unit, int cond, int width, int client, size_t n, const uint32_t *d_in,
                       uint32_t *d_out, Plan **out) {
     for (auto &p : plans)
       if (p->unit == unit && p->cond == cond && p->width == width && p->client == client &&
-          p->n == n && p->d_in == d_in && p->d_out == d_out && p->xp == ctx->cfg_xp) {
+          p->n == n && p->d_in == d_in && p->d_out == d_out && p->xp == ctx->cfg_xp &&
+          p->ks == ctx->cfg_ks) {
         p->last_use = ++use_clock;
         *out = p.get();
         return CE_OK;
@@ -527,6 +636,7 @@ class Engine {
     p->width = width;
     p->client = client;
     p->xp = ctx->cfg_xp;
+    p->ks = ctx->cfg_ks;
     p->n = n;
     p->d_in = d_in;
     p->d_out = d_out;
@@ -564,28 +674,10 @@ class Engine {
       s = build_tick(act, t);
       if (s != CE_OK) return s;
       for (Instance *in : act) ++in->level;
-      Plan::Level lv{};
-      lv.n_jobs = int(t.jobs.size());
-      lv.n_outs = int(t.outs.size());
-      lv.G = t.G;
-      lv.blocks = t.blocks;
-      lv.tile = t.tile;
-      lv.jsplit = t.jsplit;
-      lv.ks_planes = t.ks_planes;
-      lv.br_hankel = t.br_hankel;
       p->max_jobs = std::max(p->max_jobs, t.jobs.size());
-      lv.jobs_off = put(t.jobs.data(), t.jobs.size() * sizeof(GateJob));
-      lv.outs_off = put(t.outs.data(), t.outs.size() * sizeof(GateOut));
-      lv.bsk_off = put(t.grp_bsk.data(), t.grp_bsk.size() * sizeof(void *));
-      lv.ksk_off = put(t.tile_ksk.data(), t.tile_ksk.size() * sizeof(void *));
       // the plan keeps every slot its levels write (taken before the
       // instances release theirs below)
-      for (const GateOut &o : t.outs)
-        if (o.slot > kSlotSink) {
-          ref(SRef{o.slot, false});
-          p->slots.push_back(o.slot);
-        }
-      p->levels.push_back(lv);
+      p->levels.push_back(record_level(t, blob, p->slots));
     }
     std::vector<uint32_t> map;
     for (auto &x : inst) {
@@ -614,16 +706,8 @@ class Engine {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "copy_in");
     ++*launches;
-    for (size_t L = 0; L < p.levels.size(); ++L) {
-      const Plan::Level &lv = p.levels[L];
-      s = launch_level(reinterpret_cast<const GateJob *>(p.d_desc + lv.jobs_off), lv.n_jobs,
-                       reinterpret_cast<const GateOut *>(p.d_desc + lv.outs_off), lv.n_outs,
-                       reinterpret_cast<const uint64_t *const *>(p.d_desc + lv.bsk_off),
-                       reinterpret_cast<const uint32_t *const *>(p.d_desc + lv.ksk_off),
-                       lv.G, lv.blocks, lv.tile, lv.jsplit, lv.ks_planes, lv.br_hankel, st,
-                       launches);
-      if (s != CE_OK) return s;
-    }
+    s = launch_levels(p.levels, p.d_desc, st, launches);
+    if (s != CE_OK) return s;
     copy_out_kernel<<<unsigned(p.n * p.n_out), 128, 0, st>>>(
         reinterpret_cast<const uint32_t *>(p.d_desc + p.map_off), arena, p.d_out);
     e = cudaGetLastError();
@@ -677,6 +761,7 @@ class Engine {
   cudaEvent_t desc_ev[2] = {nullptr, nullptr};
   int desc_i = 0;
   std::list<std::unique_ptr<Plan>> plans;
+  std::list<std::unique_ptr<ProgPlan>> pplans;
   uint64_t use_clock = 0;
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;
@@ -809,7 +894,8 @@ struct Run {
   const ce_insn *code = nullptr;
   size_t n = 0, pc = 0;
   std::unique_ptr<Instance> cur;
-  ce_insn one{};  // storage for single-instruction runs (serving)
+  ce_insn one{};           // storage for single-instruction runs (serving)
+  RegFile *rf = nullptr;   // register file to use instead of the client's (planning)
 };
 
 // In-flight single instructions of the serving loop, by client.
@@ -818,7 +904,7 @@ std::map<Engine *, std::map<int, Run>> g_serve_runs;
 // Executes free instructions until one needs gates (started as an instance)
 // or the program ends.
 ce_status advance(Engine &E, Run &r) {
-  RegFile &R = E.regs(r.client);
+  RegFile &R = r.rf ? *r.rf : E.regs(r.client);
   while (!r.cur && r.pc < r.n) {
     const ce_insn &I = r.code[r.pc];
     if (I.op >= kOpcodes || I.rd >= kRegs || I.rn >= kRegs || I.rm >= kRegs || I.cond > 13)
@@ -855,7 +941,7 @@ ce_status advance(Engine &E, Run &r) {
 void retire(Engine &E, Run &r) {
   const ce_insn &I = r.code[r.pc];
   E.complete(*r.cur);
-  RegFile &R = E.regs(r.client);
+  RegFile &R = r.rf ? *r.rf : E.regs(r.client);
   // CMP: result = NZCV; ADDS/SUBS: rd bits then NZCV; SMULH/UMULH: the
   // high half of the 32-bit product; others: rd bits
   const bool flags = I.op == kCmp || I.op == kAdds || I.op == kSubs;
@@ -873,6 +959,226 @@ void retire(Engine &E, Run &r) {
     }
   r.cur.reset();
   ++r.pc;
+}
+
+// ------------------------------------------------------- program plans ---
+bool plan_matches(const ce_ctx *ctx, const ProgPlan &p, size_t n_prog, const int *clients,
+                  const ce_insn *const *progs, const size_t *lens) {
+  if (p.clients.size() != n_prog || p.xp != ctx->cfg_xp || p.ks != ctx->cfg_ks) return false;
+  for (size_t i = 0; i < n_prog; ++i) {
+    if (p.clients[i] != clients[i] || p.code[i].size() != lens[i] * sizeof(ce_insn)) return false;
+    if (lens[i] && std::memcmp(p.code[i].data(), progs[i], lens[i] * sizeof(ce_insn)) != 0)
+      return false;
+  }
+  return true;
+}
+
+// Plans a program set: runs the tick loop of exec_programs on the host
+// against plan-owned input slots, recording every tick's descriptors.
+// Malformed programs fail here, before anything is enqueued.
+ce_status make_prog_plan(Engine &E, size_t n_prog, const int *clients, const ce_insn *const *progs,
+                         const size_t *lens, ProgPlan **out) {
+  auto p = std::make_unique<ProgPlan>();
+  p->xp = E.ctx->cfg_xp;
+  p->ks = E.ctx->cfg_ks;
+  for (size_t i = 0; i < n_prog; ++i) {
+    p->clients.push_back(clients[i]);
+    const uint8_t *b = reinterpret_cast<const uint8_t *>(progs[i]);
+    p->code.emplace_back(b, b + lens[i] * sizeof(ce_insn));
+    if (std::find(p->regfiles.begin(), p->regfiles.end(), clients[i]) == p->regfiles.end())
+      p->regfiles.push_back(clients[i]);
+  }
+  const size_t nrf = p->regfiles.size();
+  ce_status s = E.reserve(E.next_slot + nrf * kRegBits + 1);
+  if (s != CE_OK) return s;
+  p->in_base = uint32_t(E.next_slot);
+  for (size_t k = 0; k < nrf * kRegBits; ++k) {
+    const uint32_t sl = uint32_t(E.next_slot++);
+    if (E.rc.size() <= sl) E.rc.resize(sl + 1, 0);
+    E.rc[sl] = 1;  // owned by the plan
+    p->slots.push_back(sl);
+  }
+  // simulated register files over the input slots (one reference each)
+  std::vector<RegFile> rf(nrf);
+  for (size_t u = 0; u < nrf; ++u) {
+    const uint32_t base = p->in_base + uint32_t(u * kRegBits);
+    for (int j = 0; j < kRegs; ++j)
+      for (int b = 0; b < kWidth; ++b) {
+        rf[u].r[j][b] = SRef{base + uint32_t(j * kWidth + b), false};
+        E.ref(rf[u].r[j][b]);
+      }
+    for (int k = 0; k < 4; ++k) {
+      rf[u].nzcv[k] = SRef{base + uint32_t(kRegs * kWidth + k), false};
+      E.ref(rf[u].nzcv[k]);
+    }
+  }
+  auto release_rf = [&] {
+    for (RegFile &R : rf) {
+      for (auto &reg : R.r)
+        for (auto &b : reg) E.unref(b);
+      for (auto &b : R.nzcv) E.unref(b);
+    }
+  };
+  std::vector<Run> runs(n_prog);
+  for (size_t i = 0; i < n_prog; ++i) {
+    runs[i].client = clients[i];
+    runs[i].code = progs[i];
+    runs[i].n = lens[i];
+    runs[i].rf = &rf[std::find(p->regfiles.begin(), p->regfiles.end(), clients[i]) -
+                     p->regfiles.begin()];
+  }
+  std::vector<uint8_t> blob;
+  auto fail = [&](ce_status st) {
+    for (Run &r : runs)
+      if (r.cur) {
+        if (!r.cur->wire.empty()) E.complete(*r.cur);
+        for (const SRef &x : r.cur->result) E.unref(x);
+      }
+    release_rf();
+    E.drop_prog_plan(*p);
+    return st;
+  };
+  for (;;) {
+    std::vector<Instance *> act;
+    for (Run &r : runs) {
+      s = advance(E, r);
+      if (s != CE_OK) return fail(s);
+      if (r.cur) act.push_back(r.cur.get());
+    }
+    if (act.empty()) break;
+    TickDesc t;
+    s = E.build_tick(act, t);
+    if (s != CE_OK) return fail(s);
+    p->max_jobs = std::max(p->max_jobs, t.jobs.size());
+    p->levels.push_back(E.record_level(t, blob, p->slots));
+    ++p->ticks;
+    for (Instance *in : act) ++in->level;
+    for (Run &r : runs)
+      if (r.cur && r.cur->level == r.cur->net->depth) retire(E, r);
+  }
+  // the plan keeps the final register references, the simulation lets go
+  for (size_t u = 0; u < nrf; ++u) {
+    std::vector<SRef> refs;
+    for (int j = 0; j < kRegs; ++j)
+      for (int b = 0; b < kWidth; ++b) refs.push_back(rf[u].r[j][b]);
+    for (int k = 0; k < 4; ++k) refs.push_back(rf[u].nzcv[k]);
+    for (const SRef &r : refs) {
+      E.ref(r);
+      if (r.slot > kSlotSink) ++p->n_out_copies;
+    }
+    p->final_refs.push_back(refs);
+  }
+  release_rf();
+  cudaError_t e = cudaSuccess;
+  if (!blob.empty()) {
+    e = dev_malloc(&p->d_desc, blob.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(p->d_desc, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess)
+    e = dev_malloc(&p->d_map, (nrf * kRegBits + p->n_out_copies) * 3 * sizeof(uint32_t));
+  if (e != cudaSuccess) return fail(cuda_error(e, "program plan upload"));
+  if (E.pplans.size() >= 8) {  // evict the least recently used program plan
+    auto lru = std::min_element(E.pplans.begin(), E.pplans.end(), [](const auto &a, const auto &b) {
+      return a->last_use < b->last_use;
+    });
+    E.drop_prog_plan(**lru);
+    E.pplans.erase(lru);
+  }
+  *out = p.get();
+  E.pplans.push_back(std::move(p));
+  return CE_OK;
+}
+
+// Enqueues the copy-in, the recorded ticks and the copy-out of a plan.
+ce_status launch_prog_plan(Engine &E, ProgPlan &p, cudaStream_t st, int *launches) {
+  const size_t n_in = p.regfiles.size() * kRegBits;
+  copy_slots_kernel<<<unsigned(n_in), 128, 0, st>>>(p.d_map, E.arena);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(e, "program copy-in");
+  ++*launches;
+  ce_status s = E.launch_levels(p.levels, p.d_desc, st, launches);
+  if (s != CE_OK) return s;
+  if (p.n_out_copies) {
+    copy_slots_kernel<<<unsigned(p.n_out_copies), 128, 0, st>>>(p.d_map + 3 * n_in, E.arena);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "program copy-out");
+    ++*launches;
+  }
+  return CE_OK;
+}
+
+// One run of a planned program set on the clients' current registers:
+// fresh slots receive the final register bits; the register files then
+// point at them.  The ticks replay as the plan's captured graph.
+ce_status run_prog_plan(Engine &E, ProgPlan &p, cudaStream_t st, int *launches) {
+  ce_ctx *ctx = E.ctx;
+  ce_status s = ensure_job_scratch(ctx, p.max_jobs);
+  if (s != CE_OK) return s;
+  const size_t nrf = p.regfiles.size();
+  std::vector<uint32_t> map;
+  map.reserve((nrf * kRegBits + p.n_out_copies) * 3);
+  for (size_t u = 0; u < nrf; ++u) {
+    const RegFile &R = E.regs(p.regfiles[u]);
+    const uint32_t base = p.in_base + uint32_t(u * kRegBits);
+    for (int k = 0; k < kRegBits; ++k) {
+      const SRef &x = k < kRegs * kWidth ? R.r[k / kWidth][k % kWidth] : R.nzcv[k - kRegs * kWidth];
+      map.insert(map.end(), {x.slot, x.neg ? 1u : 0u, base + uint32_t(k)});
+    }
+  }
+  std::vector<std::vector<SRef>> fresh(nrf);  // the registers' new references
+  for (size_t u = 0; u < nrf; ++u)
+    for (const SRef &r : p.final_refs[u]) {
+      if (r.slot <= kSlotSink) {  // constants stay constants
+        fresh[u].push_back(r);
+        continue;
+      }
+      uint32_t sl;
+      s = E.alloc(&sl);
+      if (s != CE_OK) {
+        for (auto &f : fresh)
+          for (const SRef &x : f) E.unref(x);
+        return s;
+      }
+      fresh[u].push_back(SRef{sl, false});
+      map.insert(map.end(), {r.slot, r.neg ? 1u : 0u, sl});
+    }
+  // pageable source: the copy is complete for the host when the call returns
+  cudaError_t e = cudaMemcpyAsync(p.d_map, map.data(), map.size() * sizeof(uint32_t),
+                                  cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_error(e, "program map upload");
+  if (p.exec && p.exec_gen != ctx->scratch_gen) E.drop_prog_graph(p);  // scratch replaced
+  if (!p.exec) {
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(E.cap_stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return cuda_error(e, "begin capture");
+    int cnt = 0;
+    s = launch_prog_plan(E, p, E.cap_stream, &cnt);
+    e = cudaStreamEndCapture(E.cap_stream, &g);
+    if (s != CE_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_error(e, "program graph instantiate");
+    p.graph_launches = cnt;
+    p.exec_gen = ctx->scratch_gen;
+  }
+  e = cudaGraphLaunch(p.exec, st);
+  if (e != cudaSuccess) return cuda_error(e, "program graph launch");
+  *launches += p.graph_launches;
+  for (size_t u = 0; u < nrf; ++u) {
+    RegFile &R = E.regs(p.regfiles[u]);
+    for (int k = 0; k < kRegBits; ++k) {
+      SRef &x = k < kRegs * kWidth ? R.r[k / kWidth][k % kWidth] : R.nzcv[k - kRegs * kWidth];
+      E.unref(x);
+      x = fresh[u][k];
+      if (x.slot <= kSlotSink) E.ref(x);
+    }
+  }
+  p.last_use = ++E.use_clock;
+  return CE_OK;
 }
 
 }  // namespace
@@ -962,9 +1268,26 @@ ce_status exec_programs(ce_ctx *ctx, size_t n_prog, const int *clients, const ce
     runs[i].code = progs[i];
     runs[i].n = lens[i];
   }
+  *ticks = 0;
+  if (E->use_graphs && !ctx->profile && E->trace_per_tick == 0 && timeout_ns == 0) {
+    // planned once per program set, replayed as a captured graph (a host
+    // time limit needs the eager tick loop, which checks it between ticks)
+    ProgPlan *p = nullptr;
+    for (auto &pp : E->pplans)
+      if (plan_matches(ctx, *pp, n_prog, clients, progs, lens)) p = pp.get();
+    if (!p) {
+      s = make_prog_plan(*E, n_prog, clients, progs, lens, &p);
+      if (s != CE_OK) return s;
+    }
+    int launches = 0;
+    s = run_prog_plan(*E, *p, st, &launches);
+    if (s != CE_OK) return s;
+    *ticks = p->ticks;
+    ctx->last_launches = launches;
+    return CE_OK;
+  }
   const auto t0 = std::chrono::steady_clock::now();
   int launches = 0;
-  *ticks = 0;
   // On an error return, release what unfinished instructions hold.
   struct Cleanup {
     Engine *E;

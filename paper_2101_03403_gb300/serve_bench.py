@@ -85,11 +85,17 @@ def run_load(ce, srv, clients, n: int, rate: float, rng) -> dict:
 
 
 def serve(ce, ctx, n_clients: int, n_requests: int, loads, seed: int = 20210103,
-          saturate_per_client: int = 4) -> dict:
-    """Admit the clients, measure saturated capacity, then run each offered
-    load (a fraction of that capacity) with n_requests requests."""
+          saturate_per_client: int = 4, clients=None) -> dict:
+    """Admit the clients (or use the given (id, secret key) pairs, whose
+    registers 0..3 hold values, 3 nonzero), measure saturated capacity, then
+    run each offered load (a fraction of that capacity) with n_requests
+    requests."""
     rng = np.random.default_rng(seed)
-    clients, refused, setup_s = admit_clients(ce, ctx, n_clients, seed, rng)
+    own = clients is None
+    if own:
+        clients, refused, setup_s = admit_clients(ce, ctx, n_clients, seed, rng)
+    else:
+        refused, setup_s = 0, 0.0
     srv = ce.ce_server_create(ctx)
     try:
         sat = run_load(ce, srv, clients, min(n_requests, saturate_per_client * len(clients)), 0,
@@ -100,8 +106,9 @@ def serve(ce, ctx, n_clients: int, n_requests: int, loads, seed: int = 20210103,
         stats = ce.ce_server_stats(srv)
     finally:
         ce.ce_server_destroy(srv)
-    for cid, _ in clients:
-        ce.ce_client_evict(ctx, cid)
+    if own:
+        for cid, _ in clients:
+            ce.ce_client_evict(ctx, cid)
     return {"clients_admitted": len(clients), "clients_refused": refused,
             "client_device_bytes": ce.ce_client_footprint_bytes(), "setup_s": setup_s,
             "mix": dict(MIX), "saturated": sat, "points": points,

@@ -176,3 +176,39 @@ def test_branching_errors(ce, ctx):
     with pytest.raises(ce.CeError) as ei:                   # target beyond the end
         ce.ce_exec_branching(c, cid, [ce.insn("B", imm=5)], lambda *a: True)
     assert ei.value.code == -1
+
+
+def test_program_graph_replay_equals_eager(ce, ctx, keys, second_client):
+    """Two programs on two clients (§4 "Data Processing" register machines)
+    run three times from the same encrypted registers: eager ticks, then
+    planned and captured as a CUDA graph, then replayed; every register and
+    flag ciphertext is identical across the three, and decrypts to the
+    plaintext machine's result."""
+    c, cid = ctx
+    sk, _ = keys
+    sk2, cid2 = second_client
+    rng = np.random.default_rng(2023)
+    progs = [random_program(rng, 14), random_program(rng, 10)]
+    init = [[int(x) for x in rng.integers(0, 1 << W, 8)] for _ in range(2)]
+
+    def run(graphs):
+        load_regs(ce, c, cid, sk, init[0], 45)
+        load_regs(ce, c, cid2, sk2, init[1], 46)
+        ce.ce_set_unit_graphs(c, graphs)
+        try:
+            ce.ce_exec_multi(c, [cid, cid2], [[ce.insn(*i) for i in p] for p in progs])
+        finally:
+            ce.ce_set_unit_graphs(c, True)
+        return [np.concatenate([ce.ce_reg_read(c, x, r) for r in range(8)] +
+                               [ce.ce_flags_read(c, x)]) for x in (cid, cid2)]
+
+    eager = run(False)
+    first = run(True)
+    replay = run(True)
+    for a, b, d in zip(eager, first, replay):
+        assert (a == b).all() and (a == d).all()
+    for (s, x), p, v in zip(((sk, cid), (sk2, cid2)), progs, init):
+        exp_regs, exp_nzcv = run_plain(p, v)
+        assert read_regs(ce, c, x, s) == exp_regs
+        assert [ce.ce_decrypt_bit(s, f) for f in ce.ce_flags_read(c, x)] == \
+            [(exp_nzcv >> k) & 1 for k in range(4)]

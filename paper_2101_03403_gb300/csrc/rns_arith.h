@@ -10,7 +10,8 @@
 // bits the torus result.
 //
 // Arithmetic per prime p (all 32-bit):
-//   - values are kept lazily in [0, 4p) (p < 2^28, so sums below 8p fit);
+//   - values are kept lazily below B p for a bound B <= 16 tracked at compile
+//     time (p < 2^28, so 16 p fits in 32 bits; rns_ntt.cuh);
 //   - multiplication by a fixed factor w uses Shoup's precomputed quotient
 //     w' = floor(w 2^32 / p): x w - umulhi(x, w') p lies in [0, 2p) for any
 //     32-bit x (three integer multiply-adds);
@@ -167,26 +168,12 @@ RNS_HD uint32_t fold(uint32_t s) {
   return umin(s, s - uint32_t(M) * P<Q>());
 }
 
-// x 2^-32 mod p for x < 2^59 (Montgomery): the result lies in [0, 2p).
+// x 2^-32 mod p (Montgomery) for x < 2^64 - 2^32 p: the result lies below
+// x / 2^32 + p (below 2p for x < 2^32 p).
 template <int Q>
 RNS_HD uint32_t redc(uint64_t x) {
   const uint32_t m = uint32_t(x) * NInv<Q>();
   return uint32_t((x + uint64_t(m) * P<Q>()) >> 32);
-}
-
-// Radix-2 decimation-in-frequency butterfly on values in [0, 4p): (a, b) ->
-// (a + b, (a - b) w), outputs in [0, 4p).
-template <int Q>
-RNS_HD void bfly(uint32_t &a, uint32_t &b, Tw t) {
-  const uint32_t s = a + b, d = a + 4 * P<Q>() - b;
-  a = fold<Q, 4>(s);
-  b = shoup<Q>(d, t);
-}
-template <int Q>
-RNS_HD void bfly1(uint32_t &a, uint32_t &b) {
-  const uint32_t s = a + b, d = a + 4 * P<Q>() - b;
-  a = fold<Q, 4>(s);
-  b = fold<Q, 4>(d);
 }
 
 // Low 32 bits of the centred integer V (|V| < P/2) with residues r0 (mod p0)

@@ -1,11 +1,13 @@
 """Runs one batch of bootstrapped gates through the device C-ABI call, for
 profiling a single launch of each kernel (e.g. under Nsight Compute).
 
-  python -m paper_2101_03403_gb300.profile_case --gates 608 [--reps 1] [--gpb 0]
+  python -m paper_2101_03403_gb300.profile_case --gates 608 [--reps 1] [--gpb 0] [--xp 1]
   python -m paper_2101_03403_gb300.profile_case --unit ADD --pairs 256
 
 The second form runs one eager evaluation of a functional unit on encrypted
-operand pairs (the benchmark's step for ADD with 256 pairs).
+operand pairs (the benchmark's step for ADD with 256 pairs).  --xp 1 selects
+the Toeplitz form of the external products on the tensor cores (its key is
+built by an untimed first call); --ks selects the key-switch engine.
 
 Keys come from seed 20210103; inputs are uniform 501-word ciphertexts (the
 bootstrapping path is a fixed function of any input, so timing and
@@ -26,6 +28,8 @@ def main():
     ap.add_argument("--mux", action="store_true")
     ap.add_argument("--unit", default=None, help="run a functional unit instead of gates")
     ap.add_argument("--pairs", type=int, default=256)
+    ap.add_argument("--xp", type=int, default=0, help="external-product form (1: tensor cores)")
+    ap.add_argument("--ks", type=int, default=0, help="key-switch engine (1 CUDA, 2 tensor)")
     args = ap.parse_args()
     import torch
 
@@ -35,6 +39,8 @@ def main():
     ctx = ce.ce_create(0)
     cid = ce.ce_client_admit(ctx, ck)
     ce.ce_set_blind_rotate_config(ctx, args.gpb, 0)
+    ce.ce_set_external_product_form(ctx, args.xp)
+    ce.ce_set_keyswitch_config(ctx, args.ks)
     if args.unit:
         rng = np.random.default_rng(2)
         info = ce.ce_unit_info(args.unit)
@@ -62,6 +68,9 @@ def main():
     ops = torch.from_numpy(rng.integers(0, 10, n).astype(np.uint8)).cuda()
     out = torch.empty_like(a)
     s = torch.cuda.current_stream()
+    if args.xp:   # builds the tensor form's key (kernels outside the profiled launches)
+        ce.ce_gates_batch_device(ctx, cid, ops[:1], a[:1], b[:1], out[:1], 1, s)
+        ce.ce_synchronize(ctx)
     for _ in range(args.reps):
         if args.mux:
             ce.ce_mux_batch_device(ctx, cid, a, b, c, out, n, s)

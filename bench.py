@@ -67,6 +67,23 @@ def int_peak_tops(sms: int, sm_mhz: float) -> float:
     return sms * INT_LANES_PER_SM * sm_mhz * 1e6 / 1e12
 
 
+# The unit that binds the blind rotation on GB300 (ncu: the FMA-heavy pipe
+# ~80 % busy, the ALU ~47 %, issue ~63 %) is the 16-lane integer multiply-add
+# pipe, one per scheduler: a 32-bit multiply-add holds it 2 cycles per warp,
+# its high-half and 64-bit forms 4.  The method's multiplies per thread (128
+# per gate) and CMux step: 656 Shoup products of the transforms (one high-half
+# and two low multiplies: 8 cycles), 32 key positions of six 64-bit products
+# plus one Montgomery reduction (6 x 4 + 2 + 4 = 30 cycles) and 16
+# reconstructions (a Shoup product and a 64-bit multiply-add: 12 cycles).
+MULPIPE_WARP_CYCLES_PER_STEP = 656 * 8 + 32 * 30 + 16 * 12          # 6,400
+MULPIPE_CYCLES_PER_GATE = 500 * 4 * MULPIPE_WARP_CYCLES_PER_STEP    # 12.8 M
+
+
+def mulpipe_peak(sms: int, sm_mhz: float) -> float:
+    """Multiply-pipe warp-cycles per second of the GPU (4 pipes per SM)."""
+    return sms * 4 * sm_mhz * 1e6
+
+
 KERNEL_SOURCES = ["bootstrap_kernels.cu", "rns_ntt.cuh", "rns_arith.h"]
 N_PAIRS = 256
 # External-product forms compared on one gate batch (19 tiles of 128 gates:
@@ -392,7 +409,7 @@ def run_ours(args, rank: int, world: int, local: int):
     sm_mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
     peak_tops = int_peak_tops(sms, sm_mhz)
     forms = external_product_forms(ce, ctx, cid, stream, dev, rng, d_min, d_mout, mul_n,
-                                   peak_tops) if rank == 0 else None
+                                   peak_tops, mulpipe_peak(sms, sm_mhz)) if rank == 0 else None
     programs = serving = None
     if rank == 0:
         from paper_2101_03403_gb300 import serve_bench
@@ -407,12 +424,22 @@ def run_ours(args, rank: int, world: int, local: int):
 
     br_ms, br_launches = prof["blind_rotate"]
     achieved = boots * args.steps * OPS_PER_GATE / (br_ms / 1e3) / 1e12
-    roof = {"kernel": "blind_rotate", "bound": "alu", "achieved": achieved,
-            "peak": peak_tops, "unit": "Tops/s (int32)", "frac": achieved / peak_tops,
+    mp_peak = mulpipe_peak(sms, sm_mhz)
+    mp_achieved = boots * args.steps * MULPIPE_CYCLES_PER_GATE / (br_ms / 1e3)
+    roof = {"kernel": "blind_rotate", "bound": "alu", "achieved": mp_achieved / 1e12,
+            "peak": mp_peak / 1e12, "unit": "T multiply-pipe warp-cycles/s",
+            "frac": mp_achieved / mp_peak,
             "traffic": recorded_traffic("blind_rotate", args.steps and br_launches / args.steps),
-            "peak_note": f"derived: {sms} SMs x {INT_LANES_PER_SM} int32 lanes per clock x "
+            "peak_note": f"derived: {sms} SMs x 4 integer multiply-add pipes (16 lanes) x "
                          f"{sm_mhz:.0f} MHz (median SM clock sampled in the timed region); "
-                         "work = 7 ops per transform butterfly + 2.5 per multiply-accumulate",
+                         f"work = {MULPIPE_CYCLES_PER_GATE / 1e6:.1f} M pipe warp-cycles per "
+                         "bootstrap (Shoup products 8, 64-bit key products 4, Montgomery "
+                         "reductions 6, reconstructions 12 cycles per warp); ncu: that pipe is "
+                         "~80 % busy, the binding unit",
+            "int32_issue": {"achieved": achieved, "peak": peak_tops, "unit": "Tops/s (int32)",
+                            "frac": achieved / peak_tops,
+                            "note": f"{sms} SMs x {INT_LANES_PER_SM} int32 lanes per clock; "
+                                    "work = 7 ops per butterfly + 2.5 per multiply-accumulate"},
             "launches_per_step": br_launches / args.steps,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
 
@@ -541,7 +568,8 @@ def serving_leg(ce, ctx, clients, requests: int = 256, load: float = 0.9):
             "saturated_bootstraps_per_s": res["saturated"]["bootstraps_per_s"]}
 
 
-def external_product_forms(ce, ctx, cid, stream, dev, rng, d_min, d_mout, mul_n, peak_tops):
+def external_product_forms(ce, ctx, cid, stream, dev, rng, d_min, d_mout, mul_n, peak_tops,
+                           mp_peak):
     """The blind rotation's external products in both forms on one batch of
     XP_GATES seeded gates and on the MUL-64 unit: the two-prime transform on
     the CUDA cores (default) and the Toeplitz contraction on the tensor cores.
@@ -599,10 +627,12 @@ def external_product_forms(ce, ctx, cid, stream, dev, rng, d_min, d_mout, mul_n,
                  "mul16_batch64_ms": mul_ms}
         if form == 0:
             ms = prof["blind_rotate"][0]
-            ach = n * OPS_PER_GATE / (ms / 1e3) / 1e12
-            entry["roofline"] = {"kernel": "blind_rotate", "bound": "alu", "achieved": ach,
-                                 "peak": peak_tops, "unit": "Tops/s (int32)",
-                                 "frac": ach / peak_tops}
+            ach = n * MULPIPE_CYCLES_PER_GATE / (ms / 1e3)
+            entry["roofline"] = {"kernel": "blind_rotate", "bound": "alu", "achieved": ach / 1e12,
+                                 "peak": mp_peak / 1e12, "unit": "T multiply-pipe warp-cycles/s",
+                                 "frac": ach / mp_peak,
+                                 "int32_issue_frac": n * OPS_PER_GATE / (ms / 1e3) / 1e12 /
+                                 peak_tops}
         else:
             ms, cnt = prof["external_product_mma"]
             ach = n * XP_FLOPS_PER_GATE / (ms / 1e3) / 1e12

@@ -26,10 +26,16 @@
 //   - a pre-pass extracts and rounds the coefficients into [j][output]
 //     (coalesced); the one-hot operand is written by the CTA's threads from
 //     them (three 16-byte stores per output and j), one stage read ahead.
-// One thread issues the MMAs of a stage (3 K-steps x 3 limbs) and commits
-// them to the stage's release barrier; a ring of four stages overlaps the
-// copies, the one-hot construction and the MMAs.  Every wait is bounded
-// (2 s on %globaltimer, then an error flag and an orderly exit).
+// Warp roles: four builder warps write the one-hot operand of each stage
+// into a ring of four slots and signal it on the slot's "ready" mbarrier;
+// one control warp (one thread) issues the key-limb bulk copies (the slot's
+// "full" mbarrier) and, once both operands of a stage are in, the stage's
+// MMAs (3 K-steps x 3 limbs), committed to the slot's "empty" mbarrier,
+// which releases the slot to the builders and to the next copy.  Builders
+// run up to four stages ahead of the tensor cores; no CTA-wide barrier sits
+// between stages.  The builder warps then read the accumulators from TMEM
+// (epilogue).  Every wait is bounded (2 s on %globaltimer, then an error
+// flag and an orderly exit).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -48,6 +54,8 @@ constexpr int kTcJPerStage = 2;
 constexpr int kTcK = kTcJPerStage * 3 * kKsT;  // 48
 constexpr int kTcStages = kRingN / kTcJPerStage;  // 512
 constexpr int kTcSlots = 4;
+constexpr int kTcBuilders = 4;                       // builder / epilogue warps
+constexpr int kTcThreads = 32 * (kTcBuilders + 1);   // + the control warp
 constexpr int kTcNMax = 160;
 constexpr int kTcLbo = 128;                  // bytes between K-adjacent core matrices
 constexpr int kTcSbo = (kTcK / 8) * 128;     // 768: bytes between 8-row groups
@@ -62,7 +70,7 @@ static_assert(3 * kTcNMax <= int(kTcTmemCols), "three accumulators fit in TMEM")
 struct TcSmem {
   static constexpr size_t kA = size_t(kTcSlots) * kTcABytes;
   static constexpr size_t kB = size_t(kTcSlots) * kTcBBytes;
-  static constexpr size_t kBars = 2 * kTcSlots * 8;
+  static constexpr size_t kBars = 3 * kTcSlots * 8;
   static constexpr size_t kTotal = kA + kB + kBars + 16 + 128;  // + TMEM address, abort, alignment
 };
 
@@ -118,7 +126,7 @@ __device__ __forceinline__ OutJobs out_jobs(int mode, const GateOut *outs, int o
 // grid (word tile, output tile, k split).  n_tile: outputs per tile (multiple
 // of 16, <= 160); stages_per_cta: stages of K in one CTA.  With a K split the
 // outputs were zeroed and partial sums are added atomically (exact mod 2^32).
-__global__ void __launch_bounds__(128, 1) keyswitch_tc_kernel(
+__global__ void __launch_bounds__(kTcThreads, 1) keyswitch_tc_kernel(
     const uint32_t *__restrict__ acc, const uint16_t *__restrict__ hr, int ldh,
     const uint8_t *__restrict__ planes, const GateOut *__restrict__ outs,
     uint32_t *__restrict__ out, int n_out, int mode, int n_tile, int stages_per_cta,
@@ -128,7 +136,8 @@ __global__ void __launch_bounds__(128, 1) keyswitch_tc_kernel(
   uint8_t *sa = smem;
   uint8_t *sb = smem + TcSmem::kA;
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + TcSmem::kA + TcSmem::kB);
-  uint64_t *empty = full + kTcSlots;
+  uint64_t *ready = full + kTcSlots;
+  uint64_t *empty = ready + kTcSlots;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(empty + kTcSlots);
   volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
@@ -141,6 +150,9 @@ __global__ void __launch_bounds__(128, 1) keyswitch_tc_kernel(
   if (t == 0) {
     for (int s = 0; s < kTcSlots; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(full + s)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(ready + s)),
+                   "r"(kTcBuilders)
+                   : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(empty + s)) : "memory");
     }
     *abort = 0;
@@ -160,106 +172,122 @@ __global__ void __launch_bounds__(128, 1) keyswitch_tc_kernel(
   const uint32_t idesc = instr_desc(n_tile);
   const int col_stride = (n_tile + 31) & ~31;  // TMEM columns per limb accumulator
 
-  // Thread 0's record of the pipeline: stages whose key copy was issued, whose
-  // copy was seen complete, and whose MMAs were committed.
+  // The control thread's record of the pipeline: stages whose key copy was
+  // issued, whose copy was seen complete, and whose MMAs were committed.
+  const bool control = warp == kTcBuilders;
   int issued = 0, landed = 0, committed = 0;
-  if (t == 0)
+  if (control && lane == 0) {
     for (int s = 0; s < kTcSlots && s < n_stages; ++s, ++issued)
       issue_stage_copy(sa + size_t(s) * kTcABytes, smem_u32(full + s),
                        a_src + size_t(s) * kTcABytes);
-
-  // Rounded coefficients of this thread's items (item it: j' = it / n_tile,
-  // output o0 + it % n_tile), loaded one stage ahead; 0xFFFFFFFF marks a
-  // padding row (all-zero one-hot).
-  constexpr int kItems = (2 * kTcNMax + 127) / 128;
-  auto load_h = [&](int stage, uint32_t (&hv)[kItems]) {
+    for (int i = 0; i < n_stages && !*abort; ++i) {
+      const int slot = i % kTcSlots;
+      const uint32_t par = uint32_t(i / kTcSlots) & 1u;
+      if (!mbar_wait(smem_u32(full + slot), par, abort, err)) break;
+      ++landed;
+      if (!mbar_wait(smem_u32(ready + slot), par, abort, err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(sa + size_t(slot) * kTcABytes);
+      const uint32_t b0 = smem_u32(sb + size_t(slot) * kTcBBytes);
 #pragma unroll
-    for (int u = 0; u < kItems; ++u) {
-      const int it = t + 128 * u;
-      hv[u] = 0xFFFFFFFFu;
-      if (it < 2 * n_tile && stage < n_stages) {
-        const int jj = it >= n_tile, ol = it - jj * n_tile, o = o0 + ol;
-        if (o < n_out) hv[u] = hr[size_t((s0 + stage) * kTcJPerStage + jj) * ldh + o];
-      }
-    }
-  };
-  uint32_t h_cur[kItems], h_next[kItems];
-  load_h(0, h_cur);
-
-  for (int i = 0; i < n_stages; ++i) {
-    const int slot = i % kTcSlots;
-    load_h(i + 1, h_next);
-    // One-hot operand of this stage: rows = outputs of the tile, K = (j', d, q).
-    uint8_t *b = sb + size_t(slot) * kTcBBytes;
+      for (int kk = 0; kk < kTcK / 16; ++kk) {
+        const uint64_t bd = smem_desc(b0 + kk * 2 * kTcLbo);
 #pragma unroll
-    for (int u = 0; u < kItems; ++u) {
-      const int it = t + 128 * u;
-      if (it >= 2 * n_tile) break;
-      const int jj = it >= n_tile, ol = it - jj * n_tile;
-      const uint32_t h = h_cur[u];
-      const bool live = h != 0xFFFFFFFFu;
-      uint8_t *row = b + (ol >> 3) * kTcSbo + (ol & 7) * 16 + jj * 3 * kTcLbo;
-#pragma unroll
-      for (int d = 1; d <= 3; ++d) {
-        uint32_t w[4];
-#pragma unroll
-        for (int pq = 0; pq < 4; ++pq) {
-          const uint32_t d0 = (h >> (14 - 2 * (2 * pq))) & 3u;
-          const uint32_t d1 = (h >> (14 - 2 * (2 * pq + 1))) & 3u;
-          const uint32_t lo = (live && d0 == uint32_t(d)) ? 0x3C00u : 0u;  // fp16 1.0
-          const uint32_t hi = (live && d1 == uint32_t(d)) ? 0x3C00u : 0u;
-          w[pq] = lo | (hi << 16);
+        for (int pl = 0; pl < 3; ++pl) {
+          const uint64_t ad = smem_desc(a0 + pl * kTcPlaneBytes + kk * 2 * kTcLbo);
+          const uint32_t accum = (i | kk) ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                  tmem + uint32_t(pl * col_stride)),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+              : "memory");
         }
-        *reinterpret_cast<uint4 *>(row + (d - 1) * kTcLbo) = make_uint4(w[0], w[1], w[2], w[3]);
       }
-    }
-#pragma unroll
-    for (int u = 0; u < kItems; ++u) h_cur[u] = h_next[u];
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (t == 0 && !*abort) {
-      if (mbar_wait(smem_u32(full + slot), uint32_t(i / kTcSlots) & 1u, abort, err)) {
-        ++landed;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_u32(sa + size_t(slot) * kTcABytes), b0 = smem_u32(b);
-#pragma unroll
-        for (int kk = 0; kk < kTcK / 16; ++kk) {
-          const uint64_t bd = smem_desc(b0 + kk * 2 * kTcLbo);
-#pragma unroll
-          for (int pl = 0; pl < 3; ++pl) {
-            const uint64_t ad = smem_desc(a0 + pl * kTcPlaneBytes + kk * 2 * kTcLbo);
-            const uint32_t accum = (i | kk) ? 1u : 0u;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
-                    tmem + uint32_t(pl * col_stride)),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
-                : "memory");
-          }
-        }
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(empty + slot))
-            : "memory");
-        ++committed;
-      }
-      // Refill the previous stage's slot once its MMAs are done.
-      if (i >= 1 && !*abort) {
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(empty + slot))
+          : "memory");
+      ++committed;
+      // Refill the previous stage's key slot once its MMAs are done (this
+      // stage's MMAs keep the tensor cores busy meanwhile).
+      if (i >= 1) {
         const int ps = (i - 1) % kTcSlots;
-        if (mbar_wait(smem_u32(empty + ps), uint32_t((i - 1) / kTcSlots) & 1u, abort, err)) {
-          const int next = i - 1 + kTcSlots;
-          if (next < n_stages) {
-            issue_stage_copy(sa + size_t(ps) * kTcABytes, smem_u32(full + ps),
-                             a_src + size_t(next) * kTcABytes);
-            ++issued;
-          }
+        if (!mbar_wait(smem_u32(empty + ps), uint32_t((i - 1) / kTcSlots) & 1u, abort, err))
+          break;
+        const int next = i - 1 + kTcSlots;
+        if (next < n_stages) {
+          issue_stage_copy(sa + size_t(ps) * kTcABytes, smem_u32(full + ps),
+                           a_src + size_t(next) * kTcABytes);
+          ++issued;
         }
       }
+    }
+  } else if (!control) {
+    // Rounded coefficients of this thread's items (item it: j' = it / n_tile,
+    // output o0 + it % n_tile), loaded one stage ahead; 0xFFFFFFFF marks a
+    // padding row (all-zero one-hot).
+    constexpr int kItems = (2 * kTcNMax + 127) / 128;
+    auto load_h = [&](int stage, uint32_t (&hv)[kItems]) {
+#pragma unroll
+      for (int u = 0; u < kItems; ++u) {
+        const int it = t + 128 * u;
+        hv[u] = 0xFFFFFFFFu;
+        if (it < 2 * n_tile && stage < n_stages) {
+          const int jj = it >= n_tile, ol = it - jj * n_tile, o = o0 + ol;
+          if (o < n_out) hv[u] = hr[size_t((s0 + stage) * kTcJPerStage + jj) * ldh + o];
+        }
+      }
+    };
+    uint32_t h_cur[kItems], h_next[kItems];
+    load_h(0, h_cur);
+    for (int i = 0; i < n_stages; ++i) {
+      const int slot = i % kTcSlots;
+      load_h(i + 1, h_next);
+      if (i >= kTcSlots) {  // the slot's previous one-hot tile is consumed
+        bool ok = true;
+        if (lane == 0)
+          ok = mbar_wait(smem_u32(empty + slot), uint32_t((i - kTcSlots) / kTcSlots) & 1u, abort,
+                         err);
+        if (!__shfl_sync(0xFFFFFFFFu, ok, 0)) break;
+      }
+      // One-hot operand of this stage: rows = outputs of the tile, K = (j', d, q).
+      uint8_t *b = sb + size_t(slot) * kTcBBytes;
+#pragma unroll
+      for (int u = 0; u < kItems; ++u) {
+        const int it = t + 128 * u;
+        if (it >= 2 * n_tile) break;
+        const int jj = it >= n_tile, ol = it - jj * n_tile;
+        const uint32_t h = h_cur[u];
+        const bool live = h != 0xFFFFFFFFu;
+        uint8_t *row = b + (ol >> 3) * kTcSbo + (ol & 7) * 16 + jj * 3 * kTcLbo;
+#pragma unroll
+        for (int d = 1; d <= 3; ++d) {
+          uint32_t w[4];
+#pragma unroll
+          for (int pq = 0; pq < 4; ++pq) {
+            const uint32_t d0 = (h >> (14 - 2 * (2 * pq))) & 3u;
+            const uint32_t d1 = (h >> (14 - 2 * (2 * pq + 1))) & 3u;
+            const uint32_t lo = (live && d0 == uint32_t(d)) ? 0x3C00u : 0u;  // fp16 1.0
+            const uint32_t hi = (live && d1 == uint32_t(d)) ? 0x3C00u : 0u;
+            w[pq] = lo | (hi << 16);
+          }
+          *reinterpret_cast<uint4 *>(row + (d - 1) * kTcLbo) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kItems; ++u) h_cur[u] = h_next[u];
+      // make the generic-proxy stores visible to the tensor cores, then one
+      // arrival per warp
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(ready + slot))
+                     : "memory");
     }
   }
-  // The last stage's release barrier completes when every MMA has finished.
   __syncthreads();
-  if (t == 0 && *abort) {
+  if (control && lane == 0 && *abort) {
     // Orderly exit after an expired wait: let issued copies land and the
     // committed MMAs finish before shared memory and TMEM are released.
     for (int s = landed; s < issued; ++s)
@@ -269,10 +297,16 @@ __global__ void __launch_bounds__(128, 1) keyswitch_tc_kernel(
                  uint32_t((committed - 1) / kTcSlots) & 1u);
   }
   __syncthreads();
-  bool ok = !*abort;
+  // The last stage's release barrier completes when every MMA has finished
+  // (one waiting lane per builder warp; the TMEM loads below need the whole
+  // warp to agree).
+  bool ok = !*abort && !control;
   if (ok && n_stages > 0) {
     const int last = n_stages - 1;
-    ok = mbar_wait(smem_u32(empty + last % kTcSlots), uint32_t(last / kTcSlots) & 1u, abort, err);
+    if (lane == 0)
+      ok = mbar_wait(smem_u32(empty + last % kTcSlots), uint32_t(last / kTcSlots) & 1u, abort,
+                     err);
+    ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {
@@ -425,7 +459,7 @@ cudaError_t launch_keyswitch_tc(const uint32_t *acc, const uint16_t *planes, con
                                        int(TcSmem::kTotal));
   if (e != cudaSuccess) return e;
   const dim3 grid(kTcWordTiles, out_tiles, ksplit);
-  keyswitch_tc_kernel<<<grid, 128, TcSmem::kTotal, st>>>(
+  keyswitch_tc_kernel<<<grid, kTcThreads, TcSmem::kTotal, st>>>(
       acc, h, ldh, reinterpret_cast<const uint8_t *>(planes), outs, out, n_out, mode, n_tile,
       kTcStages / ksplit, err);
   return cudaGetLastError();

@@ -77,6 +77,12 @@ def int_peak_tops(sms: int, sm_mhz: float) -> float:
 # reconstructions (a Shoup product and a 64-bit multiply-add: 12 cycles).
 MULPIPE_WARP_CYCLES_PER_STEP = 656 * 8 + 32 * 30 + 16 * 12          # 6,400
 MULPIPE_CYCLES_PER_GATE = 500 * 4 * MULPIPE_WARP_CYCLES_PER_STEP    # 12.8 M
+# The same multiplies counted by kind, per thread and CMux step: 32-bit
+# multiply-adds (two per Shoup product, one per Montgomery reduction), high
+# halves (one per Shoup product), 64-bit products (key products, Montgomery
+# reductions, reconstructions).
+MUL_COUNTS_PER_THREAD_STEP = {"imad": 2 * 656 + 32 + 2 * 16, "imad_hi": 656 + 16,
+                              "imad_wide": 6 * 32 + 32 + 16}
 
 
 def mulpipe_peak(sms: int, sm_mhz: float) -> float:
@@ -424,6 +430,11 @@ def run_ours(args, rank: int, world: int, local: int):
 
     br_ms, br_launches = prof["blind_rotate"]
     achieved = boots * args.steps * OPS_PER_GATE / (br_ms / 1e3) / 1e12
+    # the same bound from the pipe's measured rates on this GPU
+    rates = ce.ce_probe_int_pipes(ctx)
+    sm_cycles_per_gate = 128 * 500 * sum(n / rates[k] for k, n in MUL_COUNTS_PER_THREAD_STEP.items())
+    measured_bound = sms * sm_mhz * 1e6 / sm_cycles_per_gate
+    measured_gps = boots * args.steps / (br_ms / 1e3)
     mp_peak = mulpipe_peak(sms, sm_mhz)
     mp_achieved = boots * args.steps * MULPIPE_CYCLES_PER_GATE / (br_ms / 1e3)
     roof = {"kernel": "blind_rotate", "bound": "alu", "achieved": mp_achieved / 1e12,
@@ -436,6 +447,12 @@ def run_ours(args, rank: int, world: int, local: int):
                          "bootstrap (Shoup products 8, 64-bit key products 4, Montgomery "
                          "reductions 6, reconstructions 12 cycles per warp); ncu: that pipe is "
                          "~80 % busy, the binding unit",
+            "measured_pipe": {"lane_ops_per_clock_per_sm": rates,
+                              "bound_gates_per_s": measured_bound,
+                              "blind_rotation_gates_per_s": measured_gps,
+                              "frac": measured_gps / measured_bound,
+                              "note": "the method's multiplies per bootstrap at the rates "
+                                      "ce_probe_int_pipes measures on this GPU"},
             "int32_issue": {"achieved": achieved, "peak": peak_tops, "unit": "Tops/s (int32)",
                             "frac": achieved / peak_tops,
                             "note": f"{sms} SMs x {INT_LANES_PER_SM} int32 lanes per clock; "

@@ -513,6 +513,14 @@ ce_status ce_trace_enable(ce_ctx *ctx, int per_tick, size_t cap);
 ce_status ce_trace_read(ce_ctx *ctx, ce_trace_rec *out, size_t cap, size_t *count,
                         uint64_t *seen);
 
+/* Measurement of the integer multiply-add pipe (the paper has no counterpart;
+ * the blind rotation's binding unit): every SM runs chained operations of
+ * three kinds — 32-bit multiply-add, high half of a 32 x 32-bit product, and
+ * 32 x 32 -> 64-bit multiply-add — timed with the SM clock, and writes the
+ * lane operations per clock per SM of each kind into lane_ops_per_clock[3].
+ * Blocking; takes about a millisecond. */
+ce_status ce_probe_int_pipes(ce_ctx *ctx, double *lane_ops_per_clock);
+
 /* Per-kernel timing for measurement: while enabled, every kernel launch of
  * the gate path is bracketed by CUDA events on its own stream.
  * ce_profile_read waits for them and returns, per kernel kind (0 = linear

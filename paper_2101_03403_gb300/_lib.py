@@ -97,6 +97,7 @@ def lib() -> ctypes.CDLL:
         "ce_autotune": (i32, [vp, i32, vp, vp, i32, ctypes.POINTER(i32)]),
         "ce_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), i32]),
         "ce_trace_enable": (i32, [vp, i32, sz]),
+        "ce_probe_int_pipes": (i32, [vp, ctypes.POINTER(ctypes.c_double)]),
         "ce_trace_read": (i32, [vp, vp, sz, ctypes.POINTER(sz), ctypes.POINTER(u64)]),
     }
     for name, (res, args) in sig.items():
@@ -345,6 +346,14 @@ TRACE_DTYPE = np.dtype([("op", "<i4"), ("neg", "<i4", 3), ("client", "<i4"), ("t
                         ("index", "<u4"), ("pad", "<u4"), ("inp", "<u4", (3, LWE_WORDS)),
                         ("out", "<u4", LWE_WORDS)])
 assert TRACE_DTYPE.itemsize == 8048
+
+
+def ce_probe_int_pipes(ctx: Context) -> dict:
+    """Measured lane operations per clock per SM of the integer multiply-add
+    pipe: 32-bit multiply-add, high-half multiply, 64-bit-result multiply-add."""
+    out = (ctypes.c_double * 3)()
+    _check(lib().ce_probe_int_pipes(ctx.ptr, out), "ce_probe_int_pipes")
+    return {"imad": out[0], "imad_hi": out[1], "imad_wide": out[2]}
 
 
 def ce_trace_enable(ctx: Context, per_tick: int, cap: int = 4096):

@@ -578,6 +578,54 @@ extern "C" ce_status ce_selftest_device_wait(ce_ctx *ctx, uint64_t limit_ns) {
   return CE_OK;
 }
 
+extern "C" ce_status ce_probe_int_pipes(ce_ctx *ctx, double *lane_ops_per_clock) {
+  if (!ctx || !lane_ops_per_clock) return set_error(CE_EINVAL, "ce_probe_int_pipes: bad argument");
+  cudaSetDevice(ctx->device);
+  CtxWork work(ctx, ctx->stream);
+  // one 512-thread block per SM (16 warps, eight independent chains each)
+  const int blocks = ctx->sms, iters = 4096, threads = 512;
+  uint32_t *sink = nullptr;
+  long long *cyc = nullptr;
+  int *smid = nullptr;
+  cudaError_t e = dev_malloc(&sink, size_t(blocks) * threads * sizeof(uint32_t));
+  if (e == cudaSuccess) e = dev_malloc(&cyc, size_t(blocks) * sizeof(long long));
+  if (e == cudaSuccess) e = dev_malloc(&smid, size_t(blocks) * sizeof(int));
+  std::vector<long long> h(blocks);
+  std::vector<int> hs(blocks);
+  for (int kind = 0; kind < 3 && e == cudaSuccess; ++kind) {
+    // the first launch of each kind warms up; the second is measured
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep)
+      e = launch_int_pipe_probe(kind, blocks, threads, iters, sink, cyc, smid, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(h.data(), cyc, blocks * sizeof(long long), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(hs.data(), smid, blocks * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) {
+      // per SM: the operations of its blocks over the longest of their times
+      std::vector<double> ops(1024, 0.0), span(1024, 0.0);
+      for (int b = 0; b < blocks; ++b) {
+        const int id = hs[b] & 1023;
+        ops[id] += double(threads) * 8.0 * iters;
+        span[id] = std::max(span[id], double(h[b]));
+      }
+      double sum = 0;
+      int used = 0;
+      for (int id = 0; id < 1024; ++id)
+        if (span[id] > 0) {
+          sum += ops[id] / span[id];
+          ++used;
+        }
+      lane_ops_per_clock[kind] = used ? sum / used : 0.0;
+    }
+  }
+  dev_free(sink);
+  dev_free(cyc);
+  dev_free(smid);
+  if (e != cudaSuccess) return cuda_fail(e, "ce_probe_int_pipes");
+  return CE_OK;
+}
+
 extern "C" ce_status ce_profile_enable(ce_ctx *ctx, int on) {
   if (!ctx) return set_error(CE_EINVAL, "ce_profile_enable: null context");
   std::lock_guard<std::recursive_mutex> lock(ctx->mu);

@@ -736,6 +736,63 @@ __global__ void wait_selftest_kernel(uint64_t limit_ns, int *err) {
   if (threadIdx.x == 0) (void)bounded_wait(smem_addr(&bar), 0u, &abort_flag, err, limit_ns);
 }
 
+// Integer multiply-add pipe probe: every thread runs eight independent chains
+// of `iters` dependent operations of one kind on per-thread operands (0:
+// 32-bit multiply-add, 1:
+// high half of a 32 x 32-bit product plus an addend, 2: 32 x 32 -> 64-bit
+// product plus a 64-bit addend) between two reads of the SM clock; block b
+// stores its cycle count and the SM it ran on.  Launched with every block
+// resident at once.
+template <int KIND>
+__global__ void __launch_bounds__(512) int_pipe_probe_kernel(uint32_t a, uint32_t b, int iters,
+                                                             uint32_t *sink, long long *cycles,
+                                                             int *smid) {
+  // per-thread operands (registers, as the transform's factors are)
+  a ^= threadIdx.x << 1;
+  b += threadIdx.x;
+  uint32_t x[8];
+  uint64_t y[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    x[k] = threadIdx.x * 2654435761u + uint32_t(k) * 7919u;
+    y[k] = x[k];
+  }
+  __syncthreads();
+  const long long t0 = clock64();
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (KIND == 0) x[k] = x[k] * a + b;
+      if (KIND == 1) x[k] = __umulhi(x[k], a) + b;
+      if (KIND == 2) y[k] = uint64_t(uint32_t(y[k])) * a + y[k];
+    }
+  }
+  __syncthreads();
+  const long long t1 = clock64();
+  uint32_t f = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) f ^= x[k] ^ uint32_t(y[k]) ^ uint32_t(y[k] >> 32);
+  sink[size_t(blockIdx.x) * blockDim.x + threadIdx.x] = f;
+  if (threadIdx.x == 0) {
+    cycles[blockIdx.x] = t1 - t0;
+    int id;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(id));
+    smid[blockIdx.x] = id;
+  }
+}
+
+cudaError_t launch_int_pipe_probe(int kind, int blocks, int threads, int iters, uint32_t *sink,
+                                  long long *cycles, int *smid, cudaStream_t st) {
+  const uint32_t a = 0x9E3779B1u, b = 0x7F4A7C15u;
+  if (kind == 0)
+    int_pipe_probe_kernel<0><<<blocks, threads, 0, st>>>(a, b, iters, sink, cycles, smid);
+  else if (kind == 1)
+    int_pipe_probe_kernel<1><<<blocks, threads, 0, st>>>(a, b, iters, sink, cycles, smid);
+  else
+    int_pipe_probe_kernel<2><<<blocks, threads, 0, st>>>(a, b, iters, sink, cycles, smid);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_wait_selftest(uint64_t limit_ns, int *err, cudaStream_t st) {
   wait_selftest_kernel<<<1, 32, 0, st>>>(limit_ns, err);
   return cudaGetLastError();

@@ -75,6 +75,13 @@ cudaError_t launch_blind_rotate_tc(const uint16_t *hankel, const uint16_t *abar,
                                    cudaStream_t st, int *launches,
                                    cudaEvent_t *mma_ev = nullptr);
 
+// Integer multiply-add pipe probe (measurement): `blocks` blocks of
+// `threads` threads (at most 512), each timing iters x 8 chained operations
+// of one kind (0 32-bit multiply-add, 1 high-half multiply, 2 64-bit-result
+// multiply-add) with the SM clock into cycles[block], its SM into smid[block].
+cudaError_t launch_int_pipe_probe(int kind, int blocks, int threads, int iters, uint32_t *sink,
+                                  long long *cycles, int *smid, cudaStream_t st);
+
 // Failure-detection self-test: a one-thread bounded wait on a barrier that
 // nothing completes, with the given limit (sets *err on expiry).
 cudaError_t launch_wait_selftest(uint64_t limit_ns, int *err, cudaStream_t st);

@@ -93,8 +93,10 @@ def mulpipe_peak(sms: int, sm_mhz: float) -> float:
 KERNEL_SOURCES = ["bootstrap_kernels.cu", "rns_ntt.cuh", "rns_arith.h"]
 N_PAIRS = 256
 # External-product forms compared on one gate batch (19 tiles of 128 gates:
-# two full waves of the tensor-core kernel's 16 x 19 CTAs on 152 SMs).
+# two whole tiles per CTA of the tensor-core kernel's stream-K schedule on 152
+# SMs) and on a mid-size batch.
 XP_GATES = 2432
+XP_MID_GATES = 1216   # 10 gate tiles of 128: the mid-size batch of the tensor form
 # Tensor (Toeplitz) form: per CMux step and gate, eight limb products of the
 # [2048 x 6144] key block with the 6144 digits, 2 flops per multiply-add.
 XP_FLOPS_PER_GATE = 500 * 2 * 2048 * 6144 * 8                  # 1.0066e11
@@ -640,8 +642,19 @@ def external_product_forms(ce, ctx, cid, stream, dev, rng, d_min, d_mout, mul_n,
         torch.cuda.synchronize(dev)
         mul_ms = statistics.median(ev_ms(mul, 2))
         mul_outs[form] = d_mout.cpu()
+        nm = XP_MID_GATES
+        om = torch.empty((nm, 501), dtype=torch.int32, device=dev)
+
+        def mid():
+            ce.ce_gates_batch_device(ctx, cid, ops[:nm], a[:nm], b[:nm], om, nm, stream)
+
+        mid()
+        mid_ms = statistics.median(ev_ms(mid, 3))
+        outs[(form, "mid")] = om.cpu()
         entry = {"gates_per_s": n / (batch_ms / 1e3), "batch_ms": batch_ms,
-                 "mul16_batch64_ms": mul_ms}
+                 "mul16_batch64_ms": mul_ms,
+                 "mid_batch": {"gates": nm, "gates_per_s": nm / (mid_ms / 1e3),
+                               "of_large_batch_rate": (nm / mid_ms) / (n / batch_ms)}}
         if form == 0:
             ms = prof["blind_rotate"][0]
             ach = n * MULPIPE_CYCLES_PER_GATE / (ms / 1e3)
@@ -665,6 +678,8 @@ def external_product_forms(ce, ctx, cid, stream, dev, rng, d_min, d_mout, mul_n,
     ce.ce_set_external_product_form(ctx, 0)
     assert torch.equal(outs[0], outs[1]), "external-product forms disagree"
     assert torch.equal(mul_outs[0], mul_outs[1]), "external-product forms disagree on MUL"
+    assert torch.equal(outs[(0, "mid")], outs[(1, "mid")]), "forms disagree on the mid batch"
+    assert torch.equal(outs[(0, "mid")], outs[0][:XP_MID_GATES]), "mid batch differs"
     res["identical_outputs"] = True
     res["gates"] = n
     return res

@@ -226,16 +226,47 @@ __global__ void __launch_bounds__(256) tt_digits_kernel(const uint32_t *__restri
 }
 
 // ------------------------------------------------------------------- MMA ---
-// grid (16 coefficient tiles, gate tiles, K split), 192 threads: warps 0-3
-// epilogue (TMEM lane quarters), warp 4 lane 0 copies, warp 5 lane 0 issues
-// MMAs.  hankel_i: the step's key sequences [r][o][limb][q][64].  With a K
-// split each CTA covers chunks_per_cta chunks of each sweep and adds its
-// partial sums atomically (exact mod 2^32).
+// Stream-K schedule.  The step's work is U = tiles x 16 coefficient tiles x
+// 48 units (2 sweeps x 24 chunks of K), ordered (gate tile, coefficient
+// tile, sweep, chunk); CTA b of the grid takes the contiguous range
+// [b U / G, (b + 1) U / G).  A piece is a maximal run of one (tile, sweep)
+// inside that range; each piece ends with an epilogue that adds its partial
+// sums into ACC, with atomics unless the CTA owns both sweeps of the tile
+// (exact mod 2^32 either way).  Every CTA gets the same amount of work up to
+// one unit, whatever the batch size: no partial last wave.
+constexpr int kTtUnitsPerSweep = kTtChunks;                  // 24
+constexpr int kTtUnitsPerTile = 2 * kTtUnitsPerSweep;        // 48
+
+struct TtPiece {
+  int tile, sweep, first, count;  // tile = gate tile * 16 + coefficient tile
+  bool shared;                    // another CTA adds into the same outputs
+};
+
+// Piece p of the range [u0, u1) (p = 0, 1, ...; count 0 past the end).
+__device__ __forceinline__ TtPiece tt_piece(long long u0, long long u1, int p) {
+  TtPiece q{0, 0, 0, 0, false};
+  const long long s0 = u0 / kTtUnitsPerSweep;
+  const long long s = s0 + p;  // global sweep-run index
+  const long long lo = s * kTtUnitsPerSweep > u0 ? s * kTtUnitsPerSweep : u0;
+  long long hi = (s + 1) * kTtUnitsPerSweep;
+  if (hi > u1) hi = u1;
+  if (hi <= lo) return q;
+  q.tile = int(s / 2);
+  q.sweep = int(s % 2);
+  q.first = int(lo % kTtUnitsPerSweep);
+  q.count = int(hi - lo);
+  const long long t0 = (long long)q.tile * kTtUnitsPerTile;
+  q.shared = !(u0 <= t0 && t0 + kTtUnitsPerTile <= u1);
+  return q;
+}
+
+// grid (G), 192 threads: warps 0-3 epilogue (TMEM lane quarters), warp 4
+// lane 0 copies, warp 5 lane 0 issues MMAs.  hankel_i: the step's key
+// sequences [r][o][limb][q][64].
 __global__ void __launch_bounds__(192, 1) tt_mma_kernel(const uint16_t *__restrict__ digits,
                                                         const uint16_t *__restrict__ hankel_i,
                                                         uint32_t *__restrict__ acc, int n_jobs,
-                                                        int n_tiles, int chunks_per_cta,
-                                                        int *__restrict__ err) {
+                                                        int n_tiles, int *__restrict__ err) {
   extern __shared__ __align__(128) uint8_t smem[];
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + TtSmem::kStages);
   uint64_t *empty = full + kTtSlots;
@@ -248,10 +279,9 @@ __global__ void __launch_bounds__(192, 1) tt_mma_kernel(const uint16_t *__restri
   volatile int *n_committed = abort + 3;
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int o = blockIdx.x / (kRingN / kTtN), n0 = (blockIdx.x % (kRingN / kTtN)) * kTtN;
-  const int T = blockIdx.y;
-  const int c0 = blockIdx.z * chunks_per_cta;
-  const int nch = chunks_per_cta, total = 2 * nch;
+  const long long U = (long long)n_tiles * kTtCoefTiles * kTtUnitsPerTile;
+  const long long u0 = U * blockIdx.x / gridDim.x, u1 = U * (blockIdx.x + 1) / gridDim.x;
+  const int total = int(u1 - u0);
 
   if (t == 0) {
     for (int s = 0; s < kTtSlots; ++s) {
@@ -279,78 +309,101 @@ __global__ void __launch_bounds__(192, 1) tt_mma_kernel(const uint16_t *__restri
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 4 && lane == 0) {
-    // Producer: chunk c = sweep * nch + local chunk; digits of limb `sweep`,
-    // key sequences of digit row r = ch / 4 starting at q0 = (n0 + k0) / 8.
-    for (int c = 0; c < total; ++c) {
-      const int slot = c % kTtSlots;
-      if (c >= kTtSlots &&
-          !bounded_wait(smem_u32(empty + slot), uint32_t(c / kTtSlots - 1) & 1u, abort, err))
-        break;
-      if (*abort) break;
-      const int sweep = c / nch, ch = c0 + c % nch;
-      const int r = ch / kTtChunksPerRow, k0 = (ch % kTtChunksPerRow) * kTtKC;
-      const int q0 = (n0 + k0) / 8;
-      uint8_t *st = smem + size_t(slot) * kTtStage;
-      const uint32_t bar = smem_u32(full + slot);
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                   "r"(uint32_t(kTtStage))
-                   : "memory");
-      bulk_copy(st, digits + ((size_t(sweep) * n_tiles + T) * kTtChunks + ch) * (kTtABytes / 2),
-                kTtABytes, bar);
+    // Producer: unit c of the range; digits of limb `sweep` (chunk ch of
+    // gate tile T), key sequences of digit row r = ch / 4 from
+    // q0 = (n0 + k0) / 8.
+    int c = 0;
+    for (int p = 0; c < total; ++p) {
+      const TtPiece pc = tt_piece(u0, u1, p);
+      const int T = pc.tile / kTtCoefTiles, ct = pc.tile % kTtCoefTiles;
+      const int o = ct / (kRingN / kTtN), n0 = (ct % (kRingN / kTtN)) * kTtN;
+      for (int i = 0; i < pc.count; ++i, ++c) {
+        const int slot = c % kTtSlots;
+        if (c >= kTtSlots &&
+            !bounded_wait(smem_u32(empty + slot), uint32_t(c / kTtSlots - 1) & 1u, abort, err))
+          break;
+        if (*abort) break;
+        const int ch = pc.first + i;
+        const int r = ch / kTtChunksPerRow, k0 = (ch % kTtChunksPerRow) * kTtKC;
+        const int q0 = (n0 + k0) / 8;
+        uint8_t *st = smem + size_t(slot) * kTtStage;
+        const uint32_t bar = smem_u32(full + slot);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"(uint32_t(kTtStage))
+                     : "memory");
+        bulk_copy(st,
+                  digits + ((size_t(pc.sweep) * n_tiles + T) * kTtChunks + ch) * (kTtABytes / 2),
+                  kTtABytes, bar);
 #pragma unroll
-      for (int a = 0; a < kTtLimbs; ++a)
-        bulk_copy(st + kTtABytes + a * kTtBLimbBytes,
-                  hankel_i + ((size_t(r * 2 + o) * kTtLimbs + a) * kTtQ + q0) * 64, kTtBLimbBytes,
-                  bar);
-      *n_issued = c + 1;
+        for (int a = 0; a < kTtLimbs; ++a)
+          bulk_copy(st + kTtABytes + a * kTtBLimbBytes,
+                    hankel_i + ((size_t(r * 2 + o) * kTtLimbs + a) * kTtQ + q0) * 64,
+                    kTtBLimbBytes, bar);
+        *n_issued = c + 1;
+      }
+      if (*abort) break;
     }
   } else if (warp == 5 && lane == 0) {
-    // MMA issuer: per chunk 16 K-steps x 4 key limbs; accumulators restart at
-    // each sweep, whose first MMA waits until the epilogue has read TMEM.
-    for (int c = 0; c < total; ++c) {
-      const int slot = c % kTtSlots;
-      if (c == nch) {
-        if (!bounded_wait(smem_u32(tmem_free), 0u, abort, err)) break;
+    // MMA issuer: per unit 16 K-steps x 4 key limbs; the accumulators restart
+    // at each piece, whose first MMA waits until the epilogue has read the
+    // previous piece out of TMEM.
+    int c = 0;
+    bool ok = true;
+    for (int p = 0; ok && c < total; ++p) {
+      const TtPiece pc = tt_piece(u0, u1, p);
+      if (p > 0) {
+        if (!bounded_wait(smem_u32(tmem_free), uint32_t(p - 1) & 1u, abort, err)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       }
-      if (!bounded_wait(smem_u32(full + slot), uint32_t(c / kTtSlots) & 1u, abort, err)) break;
-      *n_landed = c + 1;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_u32(smem + size_t(slot) * kTtStage);
-      const uint32_t b0 = a0 + kTtABytes;
-#pragma unroll
-      for (int s = 0; s < kTtKC / 16; ++s) {
-        const uint64_t ad = smem_desc(a0 + s * 256, 128, kTtASbo);
-        const uint32_t accum = (c % nch != 0 || s != 0) ? 1u : 0u;
-#pragma unroll
-        for (int a = 0; a < kTtLimbs; ++a) {
-          const uint64_t bd = smem_desc(b0 + a * kTtBLimbBytes + s * 256, 128, 128);
-          asm volatile(
-              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
-                  tmem + uint32_t(a * kTtN)),
-              "l"(ad), "l"(bd), "r"(kTtIdesc), "r"(accum)
-              : "memory");
+      for (int i = 0; i < pc.count; ++i, ++c) {
+        const int slot = c % kTtSlots;
+        if (!bounded_wait(smem_u32(full + slot), uint32_t(c / kTtSlots) & 1u, abort, err)) {
+          ok = false;
+          break;
         }
-      }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(empty + slot))
-          : "memory");
-      if ((c + 1) % nch == 0)
+        *n_landed = c + 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = smem_u32(smem + size_t(slot) * kTtStage);
+        const uint32_t b0 = a0 + kTtABytes;
+#pragma unroll
+        for (int s = 0; s < kTtKC / 16; ++s) {
+          const uint64_t ad = smem_desc(a0 + s * 256, 128, kTtASbo);
+          const uint32_t accum = (i != 0 || s != 0) ? 1u : 0u;
+#pragma unroll
+          for (int a = 0; a < kTtLimbs; ++a) {
+            const uint64_t bd = smem_desc(b0 + a * kTtBLimbBytes + s * 256, 128, 128);
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                    tmem + uint32_t(a * kTtN)),
+                "l"(ad), "l"(bd), "r"(kTtIdesc), "r"(accum)
+                : "memory");
+          }
+        }
         asm volatile(
             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(acc_full))
+                smem_u32(empty + slot))
             : "memory");
-      *n_committed = c + 1;
+        if (i + 1 == pc.count)
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  smem_u32(acc_full))
+              : "memory");
+        *n_committed = c + 1;
+      }
     }
   } else if (warp < 4) {
-    // Epilogue: warp w holds gates 32 w .. 32 w + 31 of the tile.
-    const int g = T * kTtM + warp * 32 + lane;
+    // Epilogue: warp w holds gates 32 w .. 32 w + 31 of the piece's tile.
     const uint32_t lane_base = uint32_t(warp * 32) << 16;
-    for (int sweep = 0; sweep < 2; ++sweep) {
-      if (!bounded_wait(smem_u32(acc_full), uint32_t(sweep), abort, err)) break;
+    int c = 0;
+    for (int p = 0; c < total; ++p) {
+      const TtPiece pc = tt_piece(u0, u1, p);
+      c += pc.count;
+      const int T = pc.tile / kTtCoefTiles, ct = pc.tile % kTtCoefTiles;
+      const int o = ct / (kRingN / kTtN), n0 = (ct % (kRingN / kTtN)) * kTtN;
+      const int g = T * kTtM + warp * 32 + lane;
+      if (!bounded_wait(smem_u32(acc_full), uint32_t(p) & 1u, abort, err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       for (int nb = 0; nb < kTtN / 16; ++nb) {
         uint32_t v[kTtLimbs][16];
@@ -375,10 +428,10 @@ __global__ void __launch_bounds__(192, 1) tt_mma_kernel(const uint16_t *__restri
 #pragma unroll
           for (int a = 0; a < kTtLimbs; ++a)
             x += uint32_t(__float2int_rn(__uint_as_float(v[a][j]))) << (8 * a);
-          d[j] = x << (5 * sweep);
+          d[j] = x << (5 * pc.sweep);
         }
         uint32_t *dst = acc + size_t(g) * 2 * kRingN + o * kRingN + n0 + nb * 16;
-        if (gridDim.z == 1) {
+        if (!pc.shared) {
           uint4 *d4 = reinterpret_cast<uint4 *>(dst);
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
@@ -394,7 +447,7 @@ __global__ void __launch_bounds__(192, 1) tt_mma_kernel(const uint16_t *__restri
           for (int j = 0; j < 16; ++j) atomicAdd(dst + j, d[j]);
         }
       }
-      if (sweep == 0) {
+      if (c < total) {
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0)
@@ -438,31 +491,19 @@ cudaError_t launch_bsk_to_hankel(const uint32_t *bsk, uint16_t *hankel, cudaStre
   return cudaGetLastError();
 }
 
-// K split of a launch: the split k (a divisor of the 24 chunks) with the
-// least modelled time, waves(k) x (1/k + 0.12 [k > 1]) in units of one
-// CTA's full-K work: waves(k) = ceil(16 tiles k / sms), and 0.12 is the
-// measured extra cost of a CTA whose partial sums go through atomics.
-int blind_rotate_tc_ksplit(int sms, int n_jobs) {
-  const int tiles = (n_jobs + kTtM - 1) / kTtM;
-  const int options[] = {1, 2, 3, 4, 6, 8};
-  int best = 1;
-  double best_cost = 1e30;
-  for (int k : options) {
-    const int waves = (kTtCoefTiles * tiles * k + sms - 1) / sms;
-    const double cost = waves * (1.0 / k + (k > 1 ? 0.12 : 0.0));
-    if (cost < best_cost) {
-      best = k;
-      best_cost = cost;
-    }
-  }
-  return best;
+// CTAs of a step's MMA launch: one per SM (a stream-K range each), fewer
+// only when the step has fewer units of work than SMs.
+int blind_rotate_tc_ctas(int sms, int n_jobs) {
+  const long long units =
+      (long long)((n_jobs + kTtM - 1) / kTtM) * kTtCoefTiles * kTtUnitsPerTile;
+  return int(units < sms ? units : sms);
 }
 
 cudaError_t launch_blind_rotate_tc(const uint16_t *hankel, const uint16_t *abar, uint32_t *acc,
-                                   int n_jobs, uint16_t *digits, int ksplit, int *err,
+                                   int n_jobs, uint16_t *digits, int ctas, int *err,
                                    cudaStream_t st, int *launches, cudaEvent_t *mma_ev) {
   if (n_jobs <= 0) return cudaSuccess;
-  if (ksplit < 1 || kTtChunks % ksplit) return cudaErrorInvalidValue;
+  if (ctas < 1 || ctas > blind_rotate_tc_ctas(1 << 30, n_jobs)) return cudaErrorInvalidValue;
   const int n_tiles = (n_jobs + kTtM - 1) / kTtM;
   const int dig_smem = 8 * 2 * kRingN * 4;  // 64 KB
   cudaError_t e = cudaFuncSetAttribute(tt_digits_kernel,
@@ -475,14 +516,13 @@ cudaError_t launch_blind_rotate_tc(const uint16_t *hankel, const uint16_t *abar,
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t step_words = size_t(kTtRows) * 2 * kTtLimbs * kTtQ * 64;
-  const dim3 mma_grid(kTtCoefTiles, n_tiles, ksplit);
+
   for (int i = 0; i < kLweN; ++i) {
     tt_digits_kernel<<<n_tiles * (kTtM / 8), 256, dig_smem, st>>>(acc, abar, i, n_jobs, n_tiles,
                                                                   digits);
     if (mma_ev) cudaEventRecord(mma_ev[2 * i], st);
-    tt_mma_kernel<<<mma_grid, 192, TtSmem::kTotal, st>>>(digits, hankel + size_t(i) * step_words,
-                                                         acc, n_jobs, n_tiles,
-                                                         kTtChunks / ksplit, err);
+    tt_mma_kernel<<<ctas, 192, TtSmem::kTotal, st>>>(digits, hankel + size_t(i) * step_words,
+                                                     acc, n_jobs, n_tiles, err);
     if (mma_ev) cudaEventRecord(mma_ev[2 * i + 1], st);
   }
   e = cudaGetLastError();

@@ -473,11 +473,11 @@ class Engine {
       return launch_lincomb_gather(jobs, arena, ctx->abar, n_jobs, ctx->err, st);
     });
     if (e == cudaSuccess && br_hankel) {
-      const int ksplit = blind_rotate_tc_ksplit(ctx->sms, n_jobs);
+      const int ctas = blind_rotate_tc_ctas(ctx->sms, n_jobs);
       int tc_launches = 0;
       e = timed(ctx, 1, st, [&] {
         return launch_blind_rotate_tc(br_hankel, ctx->abar, ctx->acc, n_jobs, ctx->tt_digits,
-                                      ksplit, ctx->err, st, &tc_launches, mma_events(ctx));
+                                      ctas, ctx->err, st, &tc_launches, mma_events(ctx));
       });
       keep_mma_events(ctx);
       *launches += tc_launches - 1;  // one blind-rotation launch is counted below
@@ -495,10 +495,8 @@ class Engine {
       if (e == cudaSuccess)
         e = timed(ctx, 2, st, [&] {
           return launch_keyswitch_tc(ctx->acc, ks_planes, outs, arena, n_outs, 2, n_tile,
-                                     out_tiles, split, ctx->ksh, ksh_ld(ctx->job_cap), ctx->err,
-                                     st);
+                                     out_tiles, split, ctx->err, st);
         });
-      ++*launches;  // the rounding pass
     } else {
       if (e == cudaSuccess && jsplit > 1) e = launch_zero_slots(outs, arena, n_outs, st);
       if (e == cudaSuccess)

@@ -55,10 +55,9 @@ cudaError_t launch_negacyclic_mul(const int16_t *d, const uint32_t *k, uint32_t 
 size_t keyswitch_tc_plane_bytes();
 cudaError_t launch_ksk_to_planes(const uint32_t *ksk, uint16_t *planes, cudaStream_t st);
 void keyswitch_tc_shape(int sms, int n_out, int *n_tile, int *out_tiles, int *ksplit);
-// h: scratch of [1024][ldh] uint16 (ldh >= n_out) for the rounded coefficients.
 cudaError_t launch_keyswitch_tc(const uint32_t *acc, const uint16_t *planes, const GateOut *outs,
                                 uint32_t *out, int n_out, int mode, int n_tile, int out_tiles,
-                                int ksplit, uint16_t *h, int ldh, int *err, cudaStream_t st);
+                                int ksplit, int *err, cudaStream_t st);
 
 // Blind rotation with the Toeplitz external product on the tensor cores
 // (blind_rotate_tc.cu).  hankel: the client's key as Hankel limb sequences
@@ -69,9 +68,9 @@ cudaError_t launch_keyswitch_tc(const uint32_t *acc, const uint16_t *planes, con
 size_t blind_rotate_tc_key_bytes();
 size_t blind_rotate_tc_digit_bytes(size_t n_jobs);
 cudaError_t launch_bsk_to_hankel(const uint32_t *bsk, uint16_t *hankel, cudaStream_t st);
-int blind_rotate_tc_ksplit(int sms, int n_jobs);
+int blind_rotate_tc_ctas(int sms, int n_jobs);
 cudaError_t launch_blind_rotate_tc(const uint16_t *hankel, const uint16_t *abar, uint32_t *acc,
-                                   int n_jobs, uint16_t *digits, int ksplit, int *err,
+                                   int n_jobs, uint16_t *digits, int ctas, int *err,
                                    cudaStream_t st, int *launches,
                                    cudaEvent_t *mma_ev = nullptr);
 

@@ -7,10 +7,10 @@ key's negacyclic Toeplitz blocks, key words in four balanced byte limbs and
 digits in two balanced 5-bit limbs (fp16 operands, exact fp32 sums).
 Ciphertexts must equal the oracle word for word (all of them for small
 batches, sampled ones for large), and the transform form on every output:
-across gate tiles of 128 with ragged tails, K splits of 8, 4 and 3 (the
-launcher's choice for 1, 2, and 3 or 10 tiles) and unsplit (19 tiles), zero
-rotations, MUX pairs, and the levels of a 16-bit unit run by the netlist
-engine.
+across gate tiles of 128 with ragged tails, stream-K ranges that split
+tiles between CTAs (partial sums added atomically: 1, 2, 3 and 10 tiles)
+and ranges of whole tiles (19 tiles, two per CTA), zero rotations, MUX
+pairs, and the levels of a 16-bit unit run by the netlist engine.
 """
 import numpy as np
 import pytest
@@ -133,8 +133,8 @@ def test_unit_add_tensor_form(ce, ctx, keys, pairs):
 
 
 def test_launch_count_of_tensor_form(ce, ctx):
-    """Linear combination, 1 + 2 x 500 blind-rotation launches, rounding and
-    key switch (tensor key switch from 32 outputs)."""
+    """Linear combination, 1 + 2 x 500 blind-rotation launches and the fused
+    extraction + key switch (tensor key switch from 32 outputs)."""
     c, _ = ctx
     rng = np.random.default_rng(70)
     n = 40
@@ -143,7 +143,7 @@ def test_launch_count_of_tensor_form(ce, ctx):
     ce.ce_set_external_product_form(c, 1)
     try:
         run_gates_device(ce, ctx, np.zeros(n, np.int64), a, b)
-        assert ce.ce_last_launch_count(c) == 1 + 1001 + 2
+        assert ce.ce_last_launch_count(c) == 1 + 1001 + 1
     finally:
         ce.ce_set_external_product_form(c, 0)
 

@@ -112,12 +112,17 @@ ce_status ensure_jobs(ce_ctx *ctx, size_t jobs) {
   while (cap < jobs) cap *= 2;
   dev_free(ctx->abar);  // synchronises with work still using the old scratch
   dev_free(ctx->acc);
+  dev_free(ctx->ksh);
   ctx->abar = nullptr;
   ctx->acc = nullptr;
+  ctx->ksh = nullptr;
   ctx->job_cap = 0;
   ++ctx->scratch_gen;  // captured graphs that baked in the old pointers are stale
   cudaError_t e = dev_malloc(&ctx->abar, cap * kAbarStride * sizeof(uint16_t));
   if (e == cudaSuccess) e = dev_malloc(&ctx->acc, cap * 2 * kRingN * sizeof(uint32_t));
+  // rounded coefficients of the tensor-core key switch: [1024][ksh_ld] (an
+  // engine tick pads its outputs to tiles of 16 beyond its jobs)
+  if (e == cudaSuccess) e = dev_malloc(&ctx->ksh, size_t(kRingN) * ksh_ld(cap) * sizeof(uint16_t));
   if (e != cudaSuccess) return set_error(CE_ENOMEM, "scratch allocation failed");
   ctx->job_cap = cap;
   return ensure_tt_digits(ctx, cap);
@@ -237,8 +242,10 @@ ce_status run_path(ce_ctx *ctx, Client *cl, int mode, const uint8_t *ops, const 
     }
     e = ce::timed(ctx, 2, st, [&] {
       return launch_keyswitch_tc(ctx->acc, cl->ksk_planes, nullptr, out, int(n), mode != 0 ? 1 : 0,
-                                 n_tile, out_tiles, ksplit, ctx->err, st);
+                                 n_tile, out_tiles, ksplit, ctx->ksh, ksh_ld(ctx->job_cap),
+                                 ctx->err, st);
     });
+    ++launches;  // the rounding pass
   } else {
     int tile, jsplit;
     ks_config(ctx, n, &tile, &jsplit);
@@ -329,6 +336,7 @@ extern "C" void ce_destroy(ce_ctx *ctx) {
   }
   dev_free(ctx->tw);
   dev_free(ctx->tt_digits);
+  dev_free(ctx->ksh);
   dev_free(ctx->err);
   dev_free(ctx->abar);
   dev_free(ctx->acc);

@@ -57,6 +57,7 @@ struct ce_ctx {
   int *err = nullptr;
   uint16_t *abar = nullptr;
   uint32_t *acc = nullptr;
+  uint16_t *ksh = nullptr;  // [1024][ksh_ld(job_cap)] rounded coefficients (tensor key switch)
   size_t job_cap = 0;
   uint64_t scratch_gen = 0;  // bumped whenever abar/acc are reallocated
   uint8_t *io_ops = nullptr;
@@ -87,6 +88,8 @@ ce_status cuda_error(cudaError_t e, const char *where);
 ce_status ensure_job_scratch(ce_ctx *ctx, size_t jobs);
 cudaEvent_t take_event(ce_ctx *ctx);
 void br_shape(const ce_ctx *ctx, size_t jobs, int *G, int *blocks);
+// Row stride (outputs) of the rounded-coefficient scratch for a job capacity.
+inline int ksh_ld(size_t job_cap) { return int((job_cap + 16 + 7) / 8 * 8); }
 // Whether a single-client key switch of n_out outputs runs on the tensor cores.
 bool ks_use_tensor(const ce_ctx *ctx, size_t n_out);
 void ks_shape(const ce_ctx *ctx, size_t n_out, int *tile, int *jsplit);

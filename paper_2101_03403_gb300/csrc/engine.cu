@@ -495,8 +495,10 @@ class Engine {
       if (e == cudaSuccess)
         e = timed(ctx, 2, st, [&] {
           return launch_keyswitch_tc(ctx->acc, ks_planes, outs, arena, n_outs, 2, n_tile,
-                                     out_tiles, split, ctx->err, st);
+                                     out_tiles, split, ctx->ksh, ksh_ld(ctx->job_cap), ctx->err,
+                                     st);
         });
+      ++*launches;  // the rounding pass
     } else {
       if (e == cudaSuccess && jsplit > 1) e = launch_zero_slots(outs, arena, n_outs, st);
       if (e == cudaSuccess)

@@ -23,12 +23,9 @@
 // K, SBO = 768 B between 8-row groups):
 //   - the key limbs were rearranged at admission into that layout, one
 //     contiguous 36 KB block per (word tile, stage), fetched by one bulk copy;
-//   - sample extraction and rounding happen in the builders: each builder
-//     thread owns up to three (output, j parity) items, reads its outputs'
-//     accumulator words a'_j = -A_{N-j} (a'_0 = A_0) one stage ahead,
-//     rounds them to 16 bits and writes the one-hot rows (three 16-byte
-//     stores per output and j).  Extraction, rounding and key switching are
-//     one launch.
+//   - a pre-pass extracts and rounds the coefficients into [j][output]
+//     (coalesced); the one-hot operand is written by the CTA's threads from
+//     them (three 16-byte stores per output and j), one stage read ahead.
 // Warp roles: four builder warps write the one-hot operand of each stage
 // into a ring of four slots and signal it on the slot's "ready" mbarrier;
 // one control warp (one thread) issues the key-limb bulk copies (the slot's
@@ -130,7 +127,8 @@ __device__ __forceinline__ OutJobs out_jobs(int mode, const GateOut *outs, int o
 // of 16, <= 160); stages_per_cta: stages of K in one CTA.  With a K split the
 // outputs were zeroed and partial sums are added atomically (exact mod 2^32).
 __global__ void __launch_bounds__(kTcThreads, 1) keyswitch_tc_kernel(
-    const uint32_t *__restrict__ acc, const uint8_t *__restrict__ planes, const GateOut *__restrict__ outs,
+    const uint32_t *__restrict__ acc, const uint16_t *__restrict__ hr, int ldh,
+    const uint8_t *__restrict__ planes, const GateOut *__restrict__ outs,
     uint32_t *__restrict__ out, int n_out, int mode, int n_tile, int stages_per_cta,
     int *__restrict__ err) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -227,39 +225,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) keyswitch_tc_kernel(
     }
   } else if (!control) {
     // Rounded coefficients of this thread's items (item it: j' = it / n_tile,
-    // output o0 + it % n_tile), extracted from the accumulators one stage
-    // ahead; 0xFFFFFFFF marks a padding row (all-zero one-hot).  a'_j of an
-    // output is -A_{N-j} (a'_0 = A_0) of its accumulator, or of the sum of
-    // its two for a MUX; the digits take round16(a'_j).
+    // output o0 + it % n_tile), loaded one stage ahead; 0xFFFFFFFF marks a
+    // padding row (all-zero one-hot).
     constexpr int kItems = (2 * kTcNMax + 127) / 128;
-    const uint32_t *src1[kItems];
-    const uint32_t *src2[kItems];
-#pragma unroll
-    for (int u = 0; u < kItems; ++u) {
-      const int it = t + 128 * u;
-      src1[u] = nullptr;
-      src2[u] = nullptr;
-      if (it < 2 * n_tile) {
-        const int o = o0 + it - (it >= n_tile ? n_tile : 0);
-        if (o < n_out) {
-          const OutJobs jb = out_jobs(mode, outs, o);
-          src1[u] = acc + size_t(jb.j1) * 2 * kRingN;
-          if (jb.j2 >= 0) src2[u] = acc + size_t(jb.j2) * 2 * kRingN;
-        }
-      }
-    }
     auto load_h = [&](int stage, uint32_t (&hv)[kItems]) {
 #pragma unroll
       for (int u = 0; u < kItems; ++u) {
         const int it = t + 128 * u;
         hv[u] = 0xFFFFFFFFu;
-        if (src1[u] != nullptr && stage < n_stages) {
-          const int j = (s0 + stage) * kTcJPerStage + (it >= n_tile ? 1 : 0);
-          const int idx = j == 0 ? 0 : kRingN - j;
-          uint32_t a = __ldg(src1[u] + idx);
-          if (src2[u] != nullptr) a += __ldg(src2[u] + idx);
-          if (j != 0) a = 0u - a;
-          hv[u] = (a + 0x8000u) >> 16;
+        if (it < 2 * n_tile && stage < n_stages) {
+          const int jj = it >= n_tile, ol = it - jj * n_tile, o = o0 + ol;
+          if (o < n_out) hv[u] = hr[size_t((s0 + stage) * kTcJPerStage + jj) * ldh + o];
         }
       }
     };
@@ -384,6 +360,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) keyswitch_tc_kernel(
                  : "memory");
 }
 
+// Sample extraction + rounding, h[j][o] = round16(a'_j) of output o with
+// a'_0 = A_0, a'_j = -A_{N-j} (A = the output's accumulator, or the sum of
+// its two for a MUX), stored with outputs contiguous so that the key switch
+// reads a stage's coefficients coalesced.  Block (32 outputs, 32 j): reads
+// along j, writes along o through a shared-memory transpose.
+__global__ void __launch_bounds__(256) ks_round_kernel(const uint32_t *__restrict__ acc,
+                                                       const GateOut *__restrict__ outs, int mode,
+                                                       int n_out, uint16_t *__restrict__ hr,
+                                                       int ldh) {
+  __shared__ uint16_t tile[32][33];
+  const int o0 = blockIdx.x * 32, j0 = blockIdx.y * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < 32; r += 8) {
+    const int o = o0 + r, j = j0 + tx;
+    uint16_t h = 0;
+    if (o < n_out) {
+      const OutJobs jb = out_jobs(mode, outs, o);
+      const uint32_t *A = acc + size_t(jb.j1) * 2 * kRingN;
+      uint32_t a = (j == 0) ? A[0] : 0u - A[kRingN - j];
+      if (jb.j2 >= 0) {
+        const uint32_t *A2 = acc + size_t(jb.j2) * 2 * kRingN;
+        a += (j == 0) ? A2[0] : 0u - A2[kRingN - j];
+      }
+      h = uint16_t((a + 0x8000u) >> 16);
+    }
+    tile[r][tx] = h;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int j = j0 + r, o = o0 + tx;
+    if (o < n_out) hr[size_t(j) * ldh + o] = tile[tx][r];
+  }
+}
+
 // Admission: the device key-switching key [j][q][d-1][512] (uint32) to the
 // three fp16 limb planes, tiled [word tile][stage][limb][core-matrix tile].
 // Block (word tile, stage); K within a stage is k = 24 j' + 8 (d - 1) + q,
@@ -436,18 +445,22 @@ void keyswitch_tc_shape(int sms, int n_out, int *n_tile, int *out_tiles, int *ks
 
 cudaError_t launch_keyswitch_tc(const uint32_t *acc, const uint16_t *planes, const GateOut *outs,
                                 uint32_t *out, int n_out, int mode, int n_tile, int out_tiles,
-                                int ksplit, int *err, cudaStream_t st) {
+                                int ksplit, uint16_t *h, int ldh, int *err, cudaStream_t st) {
   if (n_out <= 0) return cudaSuccess;
   if (n_tile < 16 || n_tile > kTcNMax || n_tile % 16 || ksplit < 1 || kTcStages % ksplit ||
-      size_t(out_tiles) * n_tile < size_t(n_out))
+      ldh < n_out || size_t(out_tiles) * n_tile < size_t(n_out))
     return cudaErrorInvalidValue;
+  ks_round_kernel<<<dim3((n_out + 31) / 32, kRingN / 32), 256, 0, st>>>(acc, outs, mode, n_out, h,
+                                                                         ldh);
+  cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess) return le;
   cudaError_t e = cudaFuncSetAttribute(keyswitch_tc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(TcSmem::kTotal));
   if (e != cudaSuccess) return e;
   const dim3 grid(kTcWordTiles, out_tiles, ksplit);
   keyswitch_tc_kernel<<<grid, kTcThreads, TcSmem::kTotal, st>>>(
-      acc, reinterpret_cast<const uint8_t *>(planes), outs, out, n_out, mode, n_tile,
+      acc, h, ldh, reinterpret_cast<const uint8_t *>(planes), outs, out, n_out, mode, n_tile,
       kTcStages / ksplit, err);
   return cudaGetLastError();
 }

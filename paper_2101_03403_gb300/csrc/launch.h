@@ -55,9 +55,10 @@ cudaError_t launch_negacyclic_mul(const int16_t *d, const uint32_t *k, uint32_t 
 size_t keyswitch_tc_plane_bytes();
 cudaError_t launch_ksk_to_planes(const uint32_t *ksk, uint16_t *planes, cudaStream_t st);
 void keyswitch_tc_shape(int sms, int n_out, int *n_tile, int *out_tiles, int *ksplit);
+// h: scratch of [1024][ldh] uint16 (ldh >= n_out) for the rounded coefficients.
 cudaError_t launch_keyswitch_tc(const uint32_t *acc, const uint16_t *planes, const GateOut *outs,
                                 uint32_t *out, int n_out, int mode, int n_tile, int out_tiles,
-                                int ksplit, int *err, cudaStream_t st);
+                                int ksplit, uint16_t *h, int ldh, int *err, cudaStream_t st);
 
 // Blind rotation with the Toeplitz external product on the tensor cores
 // (blind_rotate_tc.cu).  hankel: the client's key as Hankel limb sequences

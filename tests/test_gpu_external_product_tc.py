@@ -133,8 +133,8 @@ def test_unit_add_tensor_form(ce, ctx, keys, pairs):
 
 
 def test_launch_count_of_tensor_form(ce, ctx):
-    """Linear combination, 1 + 2 x 500 blind-rotation launches and the fused
-    extraction + key switch (tensor key switch from 32 outputs)."""
+    """Linear combination, 1 + 2 x 500 blind-rotation launches, rounding and
+    key switch (tensor key switch from 32 outputs)."""
     c, _ = ctx
     rng = np.random.default_rng(70)
     n = 40
@@ -143,7 +143,7 @@ def test_launch_count_of_tensor_form(ce, ctx):
     ce.ce_set_external_product_form(c, 1)
     try:
         run_gates_device(ce, ctx, np.zeros(n, np.int64), a, b)
-        assert ce.ce_last_launch_count(c) == 1 + 1001 + 1
+        assert ce.ce_last_launch_count(c) == 1 + 1001 + 2
     finally:
         ce.ce_set_external_product_form(c, 0)
 

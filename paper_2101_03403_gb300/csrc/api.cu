@@ -228,10 +228,9 @@ ce_status run_path(ce_ctx *ctx, Client *cl, int mode, const uint8_t *ops, const 
     br_config(ctx, jobs, &G, &blocks);
     e = ce::timed(ctx, 1, st, [&] {
       return launch_blind_rotate(cl->bsk, ctx->abar, ctx->acc, int(jobs), ctx->tw, ctx->err, G,
-                                 blocks, st);
+                                 blocks, st, nullptr, &launches);
     });
     if (e != cudaSuccess) return cuda_fail(e, "blind_rotate");
-    ++launches;
   }
   if (ks_use_tensor(ctx, n)) {
     int n_tile, out_tiles, ksplit;

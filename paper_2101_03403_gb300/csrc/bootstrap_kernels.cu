@@ -146,7 +146,7 @@ template <int G, int NSLOT>
 __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
     const uint64_t *__restrict__ bsk, const uint64_t *const *__restrict__ grp_bsk,
     const uint16_t *__restrict__ abar, uint32_t *__restrict__ acc_out, int n_jobs,
-    const uint4 *__restrict__ tw, int *__restrict__ err) {
+    const uint4 *__restrict__ tw, int *__restrict__ err, int key_base, int key_div) {
   using L = BrSmem<G, NSLOT>;
   extern __shared__ __align__(128) uint8_t smem[];
   uint64_t *ring = reinterpret_cast<uint64_t *>(smem);
@@ -173,11 +173,14 @@ __global__ void __launch_bounds__(128 * G, 1) blind_rotate_kernel(
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  // Key of the gate group that consumes chunk c of this block (one key per
-  // group; all gates of a group belong to the same client).
+  // Key of the gate group that consumes chunk c of this block (all gates of
+  // a group belong to the same client): grp_bsk[(key_base + first job of
+  // the group) / key_div], key_base = this launch's first job in the batch.
   auto chunk_src = [&](int c) {
     const uint64_t *key = bsk;
-    if (grp_bsk) key = grp_bsk[blockIdx.x + (c / kChunksPerGate) * gridDim.x];
+    if (grp_bsk)
+      key = grp_bsk[(key_base + (int(blockIdx.x) + (c / kChunksPerGate) * int(gridDim.x)) * G) /
+                    key_div];
     return key + size_t(c % kChunksPerGate) * kChunkWords;
   };
   if (threadIdx.x == 0) {
@@ -322,7 +325,7 @@ struct WideSmem {
 __global__ void __launch_bounds__(384, 1) blind_rotate_wide_kernel(
     const uint64_t *__restrict__ bsk, const uint64_t *const *__restrict__ gate_bsk,
     const uint16_t *__restrict__ abar, uint32_t *__restrict__ acc_out, int n_jobs,
-    const uint4 *__restrict__ tw, int *__restrict__ err) {
+    const uint4 *__restrict__ tw, int *__restrict__ err, int key_base, int key_div) {
   using L = WideSmem;
   extern __shared__ __align__(128) uint8_t smem[];
   uint64_t *slots = reinterpret_cast<uint64_t *>(smem);
@@ -338,7 +341,7 @@ __global__ void __launch_bounds__(384, 1) blind_rotate_wide_kernel(
   const int total = my_gates * kLweN;  // chunks per group
   auto chunk_src = [&](int c) {
     const int gate = blockIdx.x + (c / kLweN) * gridDim.x;
-    const uint64_t *key = gate_bsk ? gate_bsk[gate] : bsk;
+    const uint64_t *key = gate_bsk ? gate_bsk[(key_base + gate) / key_div] : bsk;
     return key + (size_t(c % kLweN) * kGadgetL + g) * kChunkWords;
   };
   if (threadIdx.x == 0) {
@@ -621,14 +624,36 @@ __global__ void __launch_bounds__(128) negacyclic_mul_kernel(const int16_t *__re
 template <int G, int NSLOT>
 cudaError_t launch_br(const uint64_t *bsk, const uint64_t *const *grp_bsk, const uint16_t *abar,
                       uint32_t *acc, int n, const uint4 *tw, int *err, int blocks,
-                      cudaStream_t st) {
+                      cudaStream_t st, int key_base, int key_div) {
   using L = BrSmem<G, NSLOT>;
   auto kern = blind_rotate_kernel<G, NSLOT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(L::kTotal));
   if (e != cudaSuccess) return e;
-  kern<<<blocks, 128 * G, L::kTotal, st>>>(bsk, grp_bsk, abar, acc, n, tw, err);
+  kern<<<blocks, 128 * G, L::kTotal, st>>>(bsk, grp_bsk, abar, acc, n, tw, err, key_base,
+                                           key_div);
   return cudaGetLastError();
+}
+
+// One launch of shape G over jobs [key_base, key_base + n) of the batch
+// (abar and acc already offset to the first of them).
+cudaError_t launch_shape(int G, const uint64_t *bsk, const uint64_t *const *grp_bsk,
+                         const uint16_t *abar, uint32_t *acc, int n, const uint4 *tw, int *err,
+                         int blocks, cudaStream_t st, int key_base, int key_div) {
+  switch (G) {
+    case 1: return launch_br<1, 2>(bsk, grp_bsk, abar, acc, n, tw, err, blocks, st, key_base, key_div);
+    case 2: return launch_br<2, 3>(bsk, grp_bsk, abar, acc, n, tw, err, blocks, st, key_base, key_div);
+    case 3: {  // one gate per block, three cooperating groups
+      cudaError_t e = cudaFuncSetAttribute(blind_rotate_wide_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           int(WideSmem::kTotal));
+      if (e != cudaSuccess) return e;
+      blind_rotate_wide_kernel<<<blocks, 384, WideSmem::kTotal, st>>>(bsk, grp_bsk, abar, acc, n,
+                                                                      tw, err, key_base, key_div);
+      return cudaGetLastError();
+    }
+    default: return launch_br<4, 3>(bsk, grp_bsk, abar, acc, n, tw, err, blocks, st, key_base, key_div);
+  }
 }
 
 }  // namespace
@@ -650,24 +675,37 @@ cudaError_t launch_lincomb_modswitch(const uint8_t *ops, const uint32_t *a, cons
   return cudaGetLastError();
 }
 
+BrSplit blind_rotate_split(int n_jobs, int G, int blocks) {
+  BrSplit s{n_jobs, 0, 0, 0};
+  const int gsz = G == 3 ? 1 : G;
+  const int groups = (n_jobs + gsz - 1) / gsz;
+  if ((G != 4 && G != 2) || blocks <= 0 || groups <= blocks || groups % blocks == 0) return s;
+  const int main_jobs = (groups / blocks) * blocks * gsz;  // the whole rounds
+  const int tail = n_jobs - main_jobs;
+  if (tail <= blocks) {  // one gate per block (latency shape): ~0.4 (G 4) / ~0.6 (G 2) of a round
+    s = BrSplit{main_jobs, tail, 3, tail};
+  } else if (G == 4 && tail <= 2 * blocks) {  // two gates per block: ~0.6 of a round
+    s = BrSplit{main_jobs, tail, 2, (tail + 1) / 2};
+  }
+  return s;
+}
+
 cudaError_t launch_blind_rotate(const uint64_t *bsk, const uint16_t *abar, uint32_t *acc,
                                 int n_jobs, const uint4 *tw, int *err, int gates_per_block,
-                                int blocks, cudaStream_t st, const uint64_t *const *grp_bsk) {
+                                int blocks, cudaStream_t st, const uint64_t *const *grp_bsk,
+                                int *launches) {
   if (n_jobs <= 0) return cudaSuccess;
-  switch (gates_per_block) {
-    case 1: return launch_br<1, 2>(bsk, grp_bsk, abar, acc, n_jobs, tw, err, blocks, st);
-    case 2: return launch_br<2, 3>(bsk, grp_bsk, abar, acc, n_jobs, tw, err, blocks, st);
-    case 3: {  // one gate per block, three cooperating groups
-      cudaError_t e = cudaFuncSetAttribute(blind_rotate_wide_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           int(WideSmem::kTotal));
-      if (e != cudaSuccess) return e;
-      blind_rotate_wide_kernel<<<blocks, 384, WideSmem::kTotal, st>>>(bsk, grp_bsk, abar, acc,
-                                                                      n_jobs, tw, err);
-      return cudaGetLastError();
-    }
-    default: return launch_br<4, 3>(bsk, grp_bsk, abar, acc, n_jobs, tw, err, blocks, st);
-  }
+  const int gsz = gates_per_block == 3 ? 1 : gates_per_block;
+  const BrSplit s = blind_rotate_split(n_jobs, gates_per_block, blocks);
+  cudaError_t e = launch_shape(gates_per_block, bsk, grp_bsk, abar, acc, s.main_jobs, tw, err,
+                               blocks, st, 0, gsz);
+  if (launches) ++*launches;
+  if (e != cudaSuccess || s.tail_jobs == 0) return e;
+  e = launch_shape(s.tail_G, bsk, grp_bsk, abar + size_t(s.main_jobs) * kAbarStride,
+                   acc + size_t(s.main_jobs) * 2 * kRingN, s.tail_jobs, tw, err, s.tail_blocks,
+                   st, s.main_jobs, gsz);
+  if (launches) ++*launches;
+  return e;
 }
 
 template <int GT>

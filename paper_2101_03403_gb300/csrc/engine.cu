@@ -482,10 +482,12 @@ class Engine {
       keep_mma_events(ctx);
       *launches += tc_launches - 1;  // one blind-rotation launch is counted below
     } else if (e == cudaSuccess) {
+      int br_launches = 0;
       e = timed(ctx, 1, st, [&] {
         return launch_blind_rotate(nullptr, ctx->abar, ctx->acc, n_jobs, ctx->tw, ctx->err, G,
-                                   blocks, st, grp_bsk);
+                                   blocks, st, grp_bsk, &br_launches);
       });
+      *launches += br_launches - 1;  // one blind-rotation launch is counted below
     }
     int split = jsplit;
     if (ks_planes) {

@@ -13,11 +13,20 @@ namespace ce {
 cudaError_t launch_lincomb_modswitch(const uint8_t *ops, const uint32_t *a, const uint32_t *b,
                                      const uint32_t *c, uint16_t *abar, int n_jobs, int mode,
                                      int *err, cudaStream_t st);
-// grp_bsk (optional): per gate-group key (group g = gates [g*G, g*G+G)).
+// grp_bsk (optional): per gate-group key (group g = gates [g*G, g*G+G);
+// G = 1 for the latency shape 3).  A batch whose groups leave a part-filled
+// last round over the blocks runs as two launches: the whole rounds in the
+// given shape, then the remaining gates in a shape with fewer gates per
+// block (blind_rotate_split; the tail's keys are looked up in the same
+// grp_bsk).  launches (optional) is incremented per kernel launched.
 cudaError_t launch_blind_rotate(const uint64_t *bsk, const uint16_t *abar, uint32_t *acc,
                                 int n_jobs, const uint4 *tw, int *err, int gates_per_block,
                                 int blocks, cudaStream_t st,
-                                const uint64_t *const *grp_bsk = nullptr);
+                                const uint64_t *const *grp_bsk = nullptr, int *launches = nullptr);
+struct BrSplit {
+  int main_jobs, tail_jobs, tail_G, tail_blocks;
+};
+BrSplit blind_rotate_split(int n_jobs, int gates_per_block, int blocks);
 size_t blind_rotate_smem_bytes(int gates_per_block);
 cudaError_t launch_extract_keyswitch(const uint32_t *acc, const uint32_t *ksk, uint32_t *out,
                                      int n_out, bool mux, int tile, int jsplit, cudaStream_t st);

@@ -93,6 +93,7 @@ extern "C" ce_status ce_gates_batch_device_noalloc(ce_ctx *ctx, int client, cons
     uint32_t *acc = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(base) + kAbarBytes);
     int G, blocks, tile, jsplit;
     gate_path_shape(ctx, n, n, &G, &blocks, &tile, &jsplit);
+    int br_launches = 0;
     // the same kinds as the allocating path, so per-kernel timing sees them
     e = timed(ctx, 0, st, [&] {
       return launch_lincomb_modswitch(d_ops, d_a, d_b, nullptr, abar, int(n), 0, res.err, st);
@@ -101,7 +102,7 @@ extern "C" ce_status ce_gates_batch_device_noalloc(ce_ctx *ctx, int client, cons
       s = fail(e, "lincomb_modswitch");
     } else if ((e = timed(ctx, 1, st, [&] {
                   return launch_blind_rotate(res.bsk, abar, acc, int(n), res.tw, res.err, G,
-                                             blocks, st);
+                                             blocks, st, nullptr, &br_launches);
                 })) != cudaSuccess) {
       s = fail(e, "blind_rotate");
     } else if (jsplit > 1 &&
@@ -114,7 +115,7 @@ extern "C" ce_status ce_gates_batch_device_noalloc(ce_ctx *ctx, int client, cons
                 })) != cudaSuccess) {
       s = fail(e, "extract_keyswitch");
     } else {
-      ctx->last_launches = 3;
+      ctx->last_launches = 2 + br_launches;
     }
   }
   if (current != res.device) cudaSetDevice(current);

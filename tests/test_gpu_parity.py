@@ -96,6 +96,41 @@ def test_launch_shapes_agree_and_match_oracle(ce, ctx, O, full_keys, gpb):
     assert (got[idx] == exp).all()
 
 
+@pytest.mark.parametrize("gpb,n", [(4, 708), (4, 808), (2, 404)])
+def test_part_filled_last_round_runs_in_a_smaller_shape(ce, ctx, O, full_keys, gpb, n):
+    """A batch whose gate groups leave the last round over the SMs part
+    filled runs its whole rounds in the chosen shape and the remaining gates
+    in a shape with fewer gates per block (one gate per block for up to one
+    gate per SM, two for up to two): outputs equal the one-gate-per-block
+    shape's everywhere and the oracle on sampled gates of both parts."""
+    import torch
+    c, cid = ctx
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    rng = np.random.default_rng(300 + n)
+    ops = rng.integers(0, 10, n)
+    a, b = random_ciphertexts(rng, n), random_ciphertexts(rng, n)
+    counts = {}
+    for shape in (gpb, 1):
+        ce.ce_set_blind_rotate_config(c, shape, 0)
+        try:
+            out = run_gates_device(ce, ctx, ops, a, b)
+            counts[shape] = ce.ce_last_launch_count(c)
+        finally:
+            ce.ce_set_blind_rotate_config(c, 0, 0)
+        if shape == gpb:
+            got = out
+    assert (got == out).all()
+    groups = -(-n // gpb)
+    whole = (groups // sms) * sms * gpb
+    tail = n - whole
+    split = groups > sms and groups % sms != 0 and (tail <= sms or (gpb == 4 and tail <= 2 * sms))
+    assert counts[gpb] == counts[1] + (1 if split else 0)
+    idx = np.unique(np.concatenate([rng.choice(n, 4, replace=False),
+                                    [0, max(whole - 1, 0), min(whole, n - 1), n - 1]]))
+    exp = O.gates(full_keys, ops[idx], a[idx], b[idx])
+    assert (got[idx] == exp).all()
+
+
 def test_host_buffer_api_matches_device_api(ce, ctx, keys, O):
     c, cid = ctx
     sk, _ = keys

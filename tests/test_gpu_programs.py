@@ -70,6 +70,50 @@ def test_programs_two_clients(ce, ctx, keys, second_client):
         assert flags == [(exp_nzcv >> k) & 1 for k in range(4)]
 
 
+def test_many_clients_in_one_level_equal_each_alone(ce, ctx, keys):
+    """Twenty clients run one ADD at once: the engine's first level holds
+    640 gates (more than one round of four-gate groups over the SMs), so the
+    blind rotation runs as whole rounds plus a tail launch that looks each
+    group's key up by its position in the batch.  Every client's result
+    register must equal, word for word, the same instruction run for that
+    client alone, and decrypt to the plaintext sum."""
+    c, cid = ctx
+    sk, _ = keys
+    rng = np.random.default_rng(77)
+    clients = [(sk, cid)]
+    extra = []
+    try:
+        for i in range(19):
+            ski = ce.ce_secret_keygen(MASTER_SEED + 200 + i)
+            cidi = ce.ce_client_admit(c, ce.ce_cloud_keygen(ski, MASTER_SEED + 200 + i))
+            extra.append(cidi)
+            clients.append((ski, cidi))
+        vals = [[int(x) for x in rng.integers(0, 1 << W, 2)] for _ in clients]
+        prog = [ce.insn("ADD", 2, 0, 1)]
+
+        def load(k):
+            ski, cidi = clients[k]
+            for r in range(2):
+                ce.ce_reg_write(c, cidi, r, np.stack(
+                    [ce.ce_encrypt_bit(ski, (vals[k][r] >> j) & 1, 90 + k, 16 * r + j)
+                     for j in range(W)]))
+
+        for k in range(len(clients)):
+            load(k)
+        ce.ce_exec_multi(c, [x[1] for x in clients], [prog] * len(clients))
+        together = [ce.ce_reg_read(c, x[1], 2).copy() for x in clients]
+        for k, (ski, cidi) in enumerate(clients):
+            load(k)
+            ce.ce_exec(c, cidi, prog)
+            alone = ce.ce_reg_read(c, cidi, 2)
+            assert (alone == together[k]).all(), k
+            got = NL.from_bits([ce.ce_decrypt_bit(ski, x) for x in alone])
+            assert got == (vals[k][0] + vals[k][1]) & 0xFFFF
+    finally:
+        for cidi in extra:
+            ce.ce_client_evict(c, cidi)
+
+
 def test_every_instruction(ce, ctx, keys):
     """Each of the machine's register instructions at least once, in a random
     order with random operands, against the plaintext model."""

@@ -73,8 +73,10 @@ cudaError_t launch_keyswitch_tc(const uint32_t *acc, const uint16_t *planes, con
 // (blind_rotate_tc.cu).  hankel: the client's key as Hankel limb sequences
 // (blind_rotate_tc_key_bytes, built by launch_bsk_to_hankel from the
 // coefficient key); digits: scratch of blind_rotate_tc_digit_bytes(n_jobs).
-// Launches 1 + 2 n kernels; ACC layout as launch_blind_rotate.  mma_ev
-// (optional, 2 n events): recorded before and after each step's MMA launch.
+// Launches 1 + 2 n kernels; ACC layout as launch_blind_rotate.  ctas: the
+// MMA launches' grid, one stream-K range each (blind_rotate_tc_ctas: one per
+// SM, fewer only for a step with fewer units than SMs).  mma_ev (optional,
+// 2 n events): recorded before and after each step's MMA launch.
 size_t blind_rotate_tc_key_bytes();
 size_t blind_rotate_tc_digit_bytes(size_t n_jobs);
 cudaError_t launch_bsk_to_hankel(const uint32_t *bsk, uint16_t *hankel, cudaStream_t st);

@@ -206,6 +206,15 @@ ce_status ce_negacyclic_mul_device(ce_ctx *ctx, const int16_t *d_d,
  * autotuned choice.  Applies to later calls. */
 ce_status ce_set_blind_rotate_config(ce_ctx *ctx, int gates_per_block,
                                      int blocks_per_sm);
+/* The launches a blind rotation of n_jobs gates makes in shape
+ * gates_per_block (1-4 as above) over `blocks` blocks (no paper passage:
+ * launch planning, callable without a GPU).  When the gate groups leave the
+ * last round over the blocks part filled (shapes 2 and 4), the whole rounds
+ * run as one launch and the remaining gates as a second one with fewer gates
+ * per block: out[0] = gates of the first launch, out[1] = gates of the
+ * second (0: none), out[2] = its shape, out[3] = its blocks.  CE_EINVAL for
+ * a null out, n_jobs < 0, a shape outside 1-4 or blocks < 1. */
+ce_status ce_blind_rotate_plan(int n_jobs, int gates_per_block, int blocks, int *out);
 /* Engine of the fused sample extraction + key switching (§3: one key switch
  * per gate): 0 = automatic (tensor cores for single-client launches of at
  * least 32 outputs, CUDA cores otherwise), 1 = CUDA cores always, 2 = tensor

@@ -67,6 +67,7 @@ def lib() -> ctypes.CDLL:
         "ce_mux_batch_device": (i32, [vp, i32, vp, vp, vp, vp, sz, vp]),
         "ce_negacyclic_mul_device": (i32, [vp, vp, vp, vp, sz, vp]),
         "ce_set_blind_rotate_config": (i32, [vp, i32, i32]),
+        "ce_blind_rotate_plan": (i32, [i32, i32, i32, ctypes.POINTER(i32)]),
         "ce_set_keyswitch_config": (i32, [vp, i32]),
         "ce_set_external_product_form": (i32, [vp, i32]),
         "ce_selftest_device_wait": (i32, [vp, ctypes.c_uint64]),
@@ -308,6 +309,15 @@ def ce_negacyclic_mul_device(ctx: Context, d_d, d_k, d_out, n: int, stream=None)
 def ce_set_blind_rotate_config(ctx: Context, gates_per_block: int, blocks_per_sm: int = 0):
     _check(lib().ce_set_blind_rotate_config(ctx.ptr, gates_per_block, blocks_per_sm),
            "ce_set_blind_rotate_config")
+
+
+def ce_blind_rotate_plan(n_jobs: int, gates_per_block: int, blocks: int) -> dict:
+    """Launches of a blind rotation of n_jobs gates: {"main_jobs", "tail_jobs",
+    "tail_shape", "tail_blocks"} (tail_jobs 0: one launch)."""
+    out = (ctypes.c_int * 4)()
+    _check(lib().ce_blind_rotate_plan(n_jobs, gates_per_block, blocks, out),
+           "ce_blind_rotate_plan")
+    return {"main_jobs": out[0], "tail_jobs": out[1], "tail_shape": out[2], "tail_blocks": out[3]}
 
 
 def ce_set_keyswitch_config(ctx: Context, engine: int):

@@ -523,6 +523,18 @@ extern "C" ce_status ce_negacyclic_mul_device(ce_ctx *ctx, const int16_t *d_d,
   return CE_OK;
 }
 
+extern "C" ce_status ce_blind_rotate_plan(int n_jobs, int gates_per_block, int blocks,
+                                          int *out) {
+  if (!out || n_jobs < 0 || gates_per_block < 1 || gates_per_block > 4 || blocks < 1)
+    return set_error(CE_EINVAL, "ce_blind_rotate_plan: bad arguments");
+  const ce::BrSplit s = ce::blind_rotate_split(n_jobs, gates_per_block, blocks);
+  out[0] = s.main_jobs;
+  out[1] = s.tail_jobs;
+  out[2] = s.tail_G;
+  out[3] = s.tail_blocks;
+  return CE_OK;
+}
+
 extern "C" ce_status ce_set_blind_rotate_config(ce_ctx *ctx, int gates_per_block,
                                                 int blocks_per_sm) {
   if (!ctx) return set_error(CE_EINVAL, "ce_set_blind_rotate_config: null context");

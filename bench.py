@@ -392,6 +392,43 @@ def run_ours(args, rank: int, world: int, local: int):
     add1_ms = alone_ms("ADD", 30)
     mul1_ms = alone_ms("MUL", 20)
 
+    def batching_leg(pairs):
+        """Level batching against one launch per gate (ce_set_level_batching):
+        the same 16-bit ADDs eagerly both ways, outputs compared word for
+        word."""
+        x = rng.integers(0, 1 << 16, (2, pairs))
+        d1 = torch.from_numpy(encrypt_operands(ce, sk, x[0], x[1], 93).view(np.int32)).to(dev)
+        outs, res = {}, {}
+        ce.ce_set_unit_graphs(ctx, False)
+        try:
+            for mode, reps in (("level_batched", 3), ("one_launch_per_gate", 2)):
+                ce.ce_set_level_batching(ctx, mode == "level_batched")
+                o1 = torch.empty((pairs, 16, 501), dtype=torch.int32, device=dev)
+                ce.ce_unit_eval_device(ctx, cid, "ADD", d1, o1, pairs, 0, stream)  # warm-up
+                torch.cuda.synchronize(dev)
+                ts = []
+                for _ in range(reps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ce.ce_unit_eval_device(ctx, cid, "ADD", d1, o1, pairs, 0, stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    ts.append(e0.elapsed_time(e1))
+                outs[mode] = o1.cpu()
+                res[mode] = {"ms": statistics.median(ts), "launches": ce.ce_last_launch_count(ctx)}
+        finally:
+            ce.ce_set_level_batching(ctx, True)
+            ce.ce_set_unit_graphs(ctx, True)
+        assert torch.equal(outs["level_batched"], outs["one_launch_per_gate"]), "batching modes differ"
+        boots = pairs * gates_per_add
+        for v in res.values():
+            v["gates_per_s"] = boots / (v["ms"] / 1e3)
+        return {"unit": "ADD", "pairs": pairs, "bootstraps": boots, **res,
+                "speedup": res["one_launch_per_gate"]["ms"] / res["level_batched"]["ms"],
+                "identical_outputs": True}
+
+    batching = batching_leg(2)
+
     # 16-bit MUL latency on 64 pairs (array multiplier)
     mul_n = 64
     ma, mb = rng.integers(0, 1 << 16, mul_n), rng.integers(0, 1 << 16, mul_n)
@@ -486,6 +523,7 @@ def run_ours(args, rank: int, world: int, local: int):
                            "parallelism": f"independent batches x{world}",
                            "graph_replay_gates_per_s": graph_value,
                            "autotuned_gates_per_block": tuned},
+                "level_batching": batching,
                 "latency_ms": {"add16_alone_p50": pct(add1_ms, 50),
                                "add16_alone_p99": pct(add1_ms, 99),
                                "add16_alone_repeats": len(add1_ms),

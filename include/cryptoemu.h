@@ -335,6 +335,15 @@ ce_status ce_unit_eval(ce_ctx *ctx, int client, int unit, int cond, int width,
  * the eager tick loop.  Program calls with a host time limit (timeout_ns >
  * 0) always run the eager tick loop. */
 ce_status ce_set_unit_graphs(ce_ctx *ctx, int on);
+/* Level batching (1, default) or, for comparison, one launch per gate and
+ * step (0): with batching off, every level of ce_unit_eval*, ce_exec* and
+ * the server runs each gate as launches of its own (its linear combination,
+ * its blind rotation in the one-gate shape, its extraction + key switch on
+ * the CUDA cores) instead of one batched launch per step.  Results are
+ * bit-identical; only the launch structure and the time change.  No paper
+ * passage: a measurement mode that sets gate-at-a-time evaluation against
+ * the level-batched engine. */
+ce_status ce_set_level_batching(ce_ctx *ctx, int on);
 
 /* ------------------------------------------- encrypted register programs --- */
 

@@ -151,6 +151,7 @@ struct RegFile {
 
 struct Plan {
   int unit = 0, cond = 0, width = 0, client = 0, xp = 0, ks = 0;
+  bool per_gate = false;             // planned for one launch per gate and step
   size_t n = 0;
   const uint32_t *d_in = nullptr;
   uint32_t *d_out = nullptr;
@@ -181,6 +182,7 @@ struct Plan {
 constexpr int kRegBits = kRegs * kWidth + 4;  // 8 x 16 register bits + NZCV
 struct ProgPlan {
   int xp = 0, ks = 0;                       // external-product form, key-switch engine
+  bool per_gate = false;                    // one launch per gate and step
   std::vector<int> clients;                 // per program
   std::vector<std::vector<uint8_t>> code;   // per program: instruction bytes
   std::vector<int> regfiles;                // distinct clients, in first-use order
@@ -361,6 +363,11 @@ class Engine {
     }
     br_shape(ctx, total_jobs, &t.G, &t.blocks);
     ks_shape(ctx, total_outs, &t.tile, &t.jsplit);
+    if (ctx->per_gate) {  // one key per job and per output: launches of one gate each
+      t.G = 3;
+      t.tile = 1;
+      t.jsplit = 1;
+    }
     t.jobs.clear();
     t.outs.clear();
     t.grp_bsk.clear();
@@ -407,9 +414,9 @@ class Engine {
     t.ks_planes = nullptr;
     t.br_hankel = nullptr;
     const bool one_client = !order.empty() && order.front()->client == order.back()->client;
-    if (one_client && ks_use_tensor(ctx, total_outs))
+    if (one_client && !ctx->per_gate && ks_use_tensor(ctx, total_outs))
       t.ks_planes = ctx->clients[order.front()->client].ksk_planes;
-    if (one_client && ctx->cfg_xp == 1) {
+    if (one_client && !ctx->per_gate && ctx->cfg_xp == 1) {
       Client &cl = ctx->clients[order.front()->client];
       ce_status hs = ensure_hankel(ctx, &cl);
       if (hs != CE_OK) return hs;
@@ -418,6 +425,7 @@ class Engine {
     // the padded batch may need more blocks than the unpadded estimate
     const size_t groups = t.jobs.size() / (t.G == 3 ? 1 : t.G);
     t.blocks = int(std::min<size_t>(groups, size_t(ctx->sms) * (t.G == 1 ? 2 : 1)));
+    if (ctx->per_gate) t.blocks = 1;
     return CE_OK;
   }
 
@@ -461,6 +469,47 @@ class Engine {
     return CE_OK;
   }
 
+  // Comparison mode (ce_set_level_batching off): every gate's steps as
+  // launches of their own — one job's gather + linear combination, one job's
+  // blind rotation (one gate, latency shape), one output's extraction + key
+  // switch — in place of the level's batched launches.  The tick was planned
+  // with one key per job and per output.
+  ce_status launch_level_per_gate(const GateJob *jobs, int n_jobs, const GateOut *outs,
+                                  int n_outs, const uint64_t *const *grp_bsk,
+                                  const uint32_t *const *tile_ksk, cudaStream_t st,
+                                  int *launches) {
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < n_jobs && e == cudaSuccess; ++k) {
+      uint16_t *abar = ctx->abar + size_t(k) * kAbarStride;
+      e = timed(ctx, 0, st, [&] {
+        return launch_lincomb_gather(jobs + k, arena, abar, 1, ctx->err, st);
+      });
+      if (e == cudaSuccess)
+        e = timed(ctx, 1, st, [&] {
+          return launch_blind_rotate(nullptr, abar, ctx->acc + size_t(k) * 2 * kRingN, 1, ctx->tw,
+                                     ctx->err, 3, 1, st, grp_bsk + k);
+        });
+      *launches += 2;
+    }
+    for (int o = 0; o < n_outs && e == cudaSuccess; ++o) {
+      e = timed(ctx, 2, st, [&] {
+        return launch_extract_keyswitch_ex(ctx->acc, nullptr, tile_ksk + o, outs + o, arena, 1, 2,
+                                           1, 1, st);
+      });
+      ++*launches;
+    }
+    if (e != cudaSuccess) return cuda_error(e, "engine per-gate launch");
+    if (trace_per_tick > 0) {
+      const int samples = std::min(trace_per_tick, n_outs);
+      trace_kernel<<<unsigned(samples), 256, 0, st>>>(jobs, outs, n_outs, samples, arena, trace_rec,
+                                                       trace_count, trace_cap, trace_tick++);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_error(e, "gate trace");
+      ++*launches;
+    }
+    return CE_OK;
+  }
+
   // Launches one level: gather + linear combination, blind rotation, key
   // switching into the arena.
   ce_status launch_level(const GateJob *jobs, int n_jobs, const GateOut *outs, int n_outs,
@@ -469,6 +518,8 @@ class Engine {
                          const uint16_t *br_hankel, cudaStream_t st, int *launches) {
     ce_status s = ensure_job_scratch(ctx, n_jobs);
     if (s != CE_OK) return s;
+    if (ctx->per_gate) return launch_level_per_gate(jobs, n_jobs, outs, n_outs, grp_bsk, tile_ksk,
+                                                    st, launches);
     cudaError_t e = timed(ctx, 0, st, [&] {
       return launch_lincomb_gather(jobs, arena, ctx->abar, n_jobs, ctx->err, st);
     });
@@ -618,7 +669,7 @@ class Engine {
     for (auto &p : plans)
       if (p->unit == unit && p->cond == cond && p->width == width && p->client == client &&
           p->n == n && p->d_in == d_in && p->d_out == d_out && p->xp == ctx->cfg_xp &&
-          p->ks == ctx->cfg_ks) {
+          p->ks == ctx->cfg_ks && p->per_gate == ctx->per_gate) {
         p->last_use = ++use_clock;
         *out = p.get();
         return CE_OK;
@@ -639,6 +690,7 @@ class Engine {
     p->client = client;
     p->xp = ctx->cfg_xp;
     p->ks = ctx->cfg_ks;
+    p->per_gate = ctx->per_gate;
     p->n = n;
     p->d_in = d_in;
     p->d_out = d_out;
@@ -966,7 +1018,9 @@ void retire(Engine &E, Run &r) {
 // ------------------------------------------------------- program plans ---
 bool plan_matches(const ce_ctx *ctx, const ProgPlan &p, size_t n_prog, const int *clients,
                   const ce_insn *const *progs, const size_t *lens) {
-  if (p.clients.size() != n_prog || p.xp != ctx->cfg_xp || p.ks != ctx->cfg_ks) return false;
+  if (p.clients.size() != n_prog || p.xp != ctx->cfg_xp || p.ks != ctx->cfg_ks ||
+      p.per_gate != ctx->per_gate)
+    return false;
   for (size_t i = 0; i < n_prog; ++i) {
     if (p.clients[i] != clients[i] || p.code[i].size() != lens[i] * sizeof(ce_insn)) return false;
     if (lens[i] && std::memcmp(p.code[i].data(), progs[i], lens[i] * sizeof(ce_insn)) != 0)
@@ -983,6 +1037,7 @@ ce_status make_prog_plan(Engine &E, size_t n_prog, const int *clients, const ce_
   auto p = std::make_unique<ProgPlan>();
   p->xp = E.ctx->cfg_xp;
   p->ks = E.ctx->cfg_ks;
+  p->per_gate = E.ctx->per_gate;
   for (size_t i = 0; i < n_prog; ++i) {
     p->clients.push_back(clients[i]);
     const uint8_t *b = reinterpret_cast<const uint8_t *>(progs[i]);
@@ -1400,6 +1455,13 @@ extern "C" ce_status ce_unit_eval_device(ce_ctx *ctx, int client, int unit, int 
                                          const uint32_t *d_in, uint32_t *d_out, size_t n,
                                          void *cuda_stream) {
   return ce_unit_eval_device_width(ctx, client, unit, cond, 16, d_in, d_out, n, cuda_stream);
+}
+
+extern "C" ce_status ce_set_level_batching(ce_ctx *ctx, int on) {
+  if (!ctx) return set_error(CE_EINVAL, "ce_set_level_batching: null context");
+  std::lock_guard<std::recursive_mutex> ctx_lock(ctx->mu);
+  ctx->per_gate = on == 0;
+  return CE_OK;
 }
 
 extern "C" ce_status ce_set_unit_graphs(ce_ctx *ctx, int on) {

@@ -118,6 +118,37 @@ def test_graph_replay_equals_eager(ce, ctx, keys):
     assert (g1 == g2).all() and (g1 == eager).all()
 
 
+@pytest.mark.parametrize("unit,cond", [("ADD", 0), ("CSEL", 12)])
+def test_one_launch_per_gate_equals_level_batching(ce, ctx, keys, unit, cond):
+    """With level batching off every gate runs as launches of its own (its
+    linear combination and one-gate blind rotation per bootstrap, its
+    extraction + key switch per gate output): the same ciphertexts as the
+    level-batched engine, MUX gates (CSEL) included, and exactly that many
+    launches plus the operand copies."""
+    c, _ = ctx
+    sk, _ = keys
+    rng = np.random.default_rng(31)
+    a, b = rng.integers(0, 1 << W, 2), rng.integers(0, 1 << W, 2)
+    f = np.array([4, 9]) if unit == "CSEL" else None   # NZCV bits N|Z<<1|C<<2|V<<3
+    inp = enc_operands(ce, sk, operand_bits(a, b, f), 12)
+    ce.ce_set_unit_graphs(c, False)
+    try:
+        batched = run_unit(ce, ctx, unit, inp, W, cond)
+        batched_launches = ce.ce_last_launch_count(c)
+        ce.ce_set_level_batching(c, False)
+        try:
+            per_gate = run_unit(ce, ctx, unit, inp, W, cond)
+            per_gate_launches = ce.ce_last_launch_count(c)
+        finally:
+            ce.ce_set_level_batching(c, True)
+    finally:
+        ce.ce_set_unit_graphs(c, True)
+    assert (per_gate == batched).all()
+    info = ce.ce_unit_info(unit, cond=cond)   # two instances: jobs = bootstraps, outputs = gates
+    assert per_gate_launches == 2 + 2 * (2 * info["n_bootstraps"]) + 2 * info["n_gates"]
+    assert per_gate_launches > 10 * batched_launches
+
+
 @pytest.mark.parametrize("unit", ["AND", "LSL", "ADD", "ASR"])
 def test_unit_ciphertexts_match_oracle(ce, ctx, keys, O, full_keys, unit):
     """One instance, every output word equal to the oracle evaluating its own

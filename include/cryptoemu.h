@@ -289,8 +289,12 @@ typedef enum {
     CE_U_SMULL = 16,      /* signed a * b, the full 2w-bit product, low half first
                              (§5 "Signed multiplication": carry-save array, sign
                              extension replaced by a constant; outputs 2w) */
-    CE_U_UMULL = 17       /* unsigned a * b, the full 2w-bit product (§5 "Unsigned
+    CE_U_UMULL = 17,      /* unsigned a * b, the full 2w-bit product (§5 "Unsigned
                              multiplication", as an array; outputs 2w) */
+    CE_U_ADD_MUX = 18,    /* ADD's parallel-prefix adder (§5 "Adder") with each span
+                             combine's carry as one MUX, G = P ? G' : G, instead of
+                             AND then OR: the same bootstraps in fewer levels */
+    CE_U_SUB_MUX = 19     /* SUB (§5 "Subtractor") with that adder */
 } ce_unit;
 
 /* Shape of a unit's netlist for width w (a power of two, 2..32). */

@@ -26,7 +26,7 @@ MUX = 10
 OPS = {"NAND": 0, "AND": 1, "OR": 2, "XOR": 3, "NOR": 4, "XNOR": 5, "ANDNY": 6, "ANDYN": 7,
        "ORNY": 8, "ORYN": 9}
 UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "CSEL", "LSR",
-         "ASR", "EOR", "ORN", "ADDS", "SUBS", "SMULL", "UMULL"]
+         "ASR", "EOR", "ORN", "ADDS", "SUBS", "SMULL", "UMULL", "ADD_MUX", "SUB_MUX"]
 CONDS = ["EQ", "NE", "CS", "CC", "MI", "PL", "VS", "VC", "HI", "LS", "GE", "LT", "GT", "LE"]
 
 
@@ -79,10 +79,13 @@ class Net:
 
 
 # --------------------------------------------------------------- adders ---
-def prefix_adder(net, a, b, carry_in=None):
+def prefix_adder(net, a, b, carry_in=None, mux_carry=False):
     """§5 "Adder": stage 1 (g, p) per bit; stage 2 Kogge-Stone combines at
     distances 1, 2, 4, ...; stage 3 sums.  carry_in: None (0), "one" (the
-    subtractor's constant 1) or an encrypted wire."""
+    subtractor's constant 1) or an encrypted wire.  mux_carry: the combined
+    G of a span is MUX(P_i; G_{i-d}, G_i) — a span whose bits all propagate
+    generates nothing itself, so this equals G_i OR (P_i AND G_{i-d}) — built
+    before the AND of the P's."""
     w = len(a)
     gen, prop = [], []
     for i in range(w):
@@ -99,9 +102,13 @@ def prefix_adder(net, a, b, carry_in=None):
         G2, P2 = list(G), list(P)
         for i in range(d, w):
             # (G_i, P_i) <- (G_i, P_i) (.) (G_{i-d}, P_{i-d})
-            t = net.g("AND", P[i], G[i - d])
-            P2[i] = net.g("AND", P[i], P[i - d])
-            G2[i] = net.g("OR", G[i], t)
+            if mux_carry:
+                G2[i] = net.mux(P[i], G[i - d], G[i])
+                P2[i] = net.g("AND", P[i], P[i - d])
+            else:
+                t = net.g("AND", P[i], G[i - d])
+                P2[i] = net.g("AND", P[i], P[i - d])
+                G2[i] = net.g("OR", G[i], t)
         G, P = G2, P2
         d *= 2
     if carry_in is None:
@@ -214,6 +221,10 @@ def build(unit: str, w: int = 16, cond: int = 0) -> Net:
         out = ripple_adder(net, a, b)
     elif unit == "SUB":
         out, _ = prefix_adder(net, a, [neg(x) for x in b], "one")
+    elif unit == "ADD_MUX":
+        out, _ = prefix_adder(net, a, b, mux_carry=True)
+    elif unit == "SUB_MUX":
+        out, _ = prefix_adder(net, a, [neg(x) for x in b], "one", mux_carry=True)
     elif unit in ("AND", "ORR"):
         out = [net.g("AND" if unit == "AND" else "OR", a[i], b[i]) for i in range(w)]
     elif unit == "EOR":
@@ -339,9 +350,9 @@ def armv8(unit: str, a: int, b: int, w: int = 16, cond: int = 0, nzcv: int = 0):
     """ARMv8 semantics truncated to w bits.  CMP returns [N, Z, C, V];
     CSEL takes nzcv as bits N|Z<<1|C<<2|V<<3."""
     m = (1 << w) - 1
-    if unit in ("ADD", "ADD_RIPPLE"):
+    if unit in ("ADD", "ADD_RIPPLE", "ADD_MUX"):
         return (a + b) & m
-    if unit == "SUB":
+    if unit in ("SUB", "SUB_MUX"):
         return (a - b) & m
     if unit == "AND":
         return a & b

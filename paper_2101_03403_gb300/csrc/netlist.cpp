@@ -68,8 +68,12 @@ struct AdderOut {
 // s_i = p_i XOR G_{i-1}.  Carry-in: constant 1 folds into bit 0 as
 // G_0 = g_0 OR p_0 and s_0 = NOT p_0 (§5 "Subtractor"); an encrypted
 // carry-in c gives G_0 = g_0 OR (p_0 AND c) and s_0 = p_0 XOR c.
+// mux_prefix: the span combine's G as one MUX, G_i <- P_i ? G_{i-d} : G_i
+// (equal to G_i OR (P_i AND G_{i-d}) because a span that propagates
+// generates nothing of its own), created before P's AND: the same
+// bootstraps in one level per span instead of two.
 AdderOut kogge_stone(Builder &B, const std::vector<Ref> &a, const std::vector<Ref> &b,
-                     int cin_kind, Ref cin) {
+                     int cin_kind, Ref cin, bool mux_prefix = false) {
   const int w = static_cast<int>(a.size());
   std::vector<Ref> g(w), p(w);
   for (int i = 0; i < w; ++i) {
@@ -86,9 +90,14 @@ AdderOut kogge_stone(Builder &B, const std::vector<Ref> &a, const std::vector<Re
   for (int d = 1; d < w; d *= 2) {
     std::vector<Ref> nG = G, nP = P;
     for (int i = d; i < w; ++i) {
-      const Ref t = B.gate(AND, P[i], G[i - d]);
-      nP[i] = B.gate(AND, P[i], P[i - d]);
-      nG[i] = B.gate(OR, G[i], t);
+      if (mux_prefix) {
+        nG[i] = B.mux(P[i], G[i - d], G[i]);
+        nP[i] = B.gate(AND, P[i], P[i - d]);
+      } else {
+        const Ref t = B.gate(AND, P[i], G[i - d]);
+        nP[i] = B.gate(AND, P[i], P[i - d]);
+        nG[i] = B.gate(OR, G[i], t);
+      }
     }
     G = nG;
     P = nP;
@@ -261,6 +270,15 @@ bool build_unit(int unit, int w, int cond, Netlist *out) {
       std::vector<Ref> nb(w);
       for (int i = 0; i < w; ++i) nb[i] = !b[i];
       o = kogge_stone(B, a, nb, 1, Ref{}).sum;
+      break;
+    }
+    case kUnitAddMux:
+      o = kogge_stone(B, a, b, 0, Ref{}, true).sum;
+      break;
+    case kUnitSubMux: {
+      std::vector<Ref> nb(w);
+      for (int i = 0; i < w; ++i) nb[i] = !b[i];
+      o = kogge_stone(B, a, nb, 1, Ref{}, true).sum;
       break;
     }
     case kUnitAnd:

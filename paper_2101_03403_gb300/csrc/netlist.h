@@ -63,7 +63,9 @@ enum Unit : int {
   kUnitSubs = 15,      // a - b and its NZCV (CMP that keeps the difference)
   kUnitSmull = 16,     // signed a * b, full 2w-bit product (§5 "Signed multiplication")
   kUnitUmull = 17,     // unsigned a * b, full 2w-bit product (§5 "Unsigned multiplication")
-  kUnitCount = 18
+  kUnitAddMux = 18,    // ADD with each span combine's carry as one MUX (fewer levels)
+  kUnitSubMux = 19,    // SUB likewise
+  kUnitCount = 20
 };
 
 // Inputs: a[width] then b[width] (CSEL: rn[width], rm[width], N, Z, C, V).

@@ -49,7 +49,8 @@ def operands(rng, n):
     return a, b
 
 
-@pytest.mark.parametrize("unit", ["ADD", "SUB", "AND", "ORR", "LSL", "LSR", "ASR", "MUL", "CMP"])
+@pytest.mark.parametrize("unit", ["ADD", "SUB", "AND", "ORR", "LSL", "LSR", "ASR", "MUL", "CMP",
+                                  "ADD_MUX", "SUB_MUX"])
 def test_unit32_semantics(ce, ctx, keys, unit):
     sk, _ = keys
     rng = np.random.default_rng(320 + NL.UNITS.index(unit))

@@ -8,7 +8,7 @@ import pytest
 from oracle import netlists as NL
 
 UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "LSR", "ASR",
-         "EOR", "ORN", "ADDS", "SUBS", "SMULL", "UMULL"]
+         "EOR", "ORN", "ADDS", "SUBS", "SMULL", "UMULL", "ADD_MUX", "SUB_MUX"]
 
 
 def eval_vec(net, inputs):
@@ -200,3 +200,19 @@ def test_library_netlist_equals_oracle(lib, unit, w):
         assert theirs["outputs"] == list(mine.outputs)
         info = lib.ce_unit_info(unit, cond, w)
         assert info["n_bootstraps"] == mine.bootstraps
+
+
+@pytest.mark.parametrize("w", [8, 16, 32])
+def test_mux_carry_adders_keep_the_bootstraps_in_fewer_levels(w):
+    """ADD_MUX / SUB_MUX: the same (g, p) stage, span distances and sums as
+    ADD / SUB, each span's carry one MUX (two bootstraps) in place of the
+    AND + OR pair: equal bootstrap counts, one level per span, so depth
+    1 + log2(w) + 1."""
+    import math
+    for fast, base in (("ADD_MUX", "ADD"), ("SUB_MUX", "SUB")):
+        f, b = NL.build(fast, w), NL.build(base, w)
+        assert f.bootstraps == b.bootstraps
+        spans = sum(w - d for d in (1 << k for k in range(int(math.log2(w)))))
+        assert sum(1 for g in f.gates if g[0] == NL.MUX) == spans
+        assert f.depth == 2 + int(math.log2(w))
+        assert b.depth > f.depth

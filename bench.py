@@ -386,13 +386,15 @@ def run_ours(args, rank: int, world: int, local: int):
             torch.cuda.synchronize(dev)
             ts.append(e0.elapsed_time(e1))
         want = {"ADD": (int(x[0]) + int(x[1])) & 0xFFFF, "MUL": (int(x[0]) * int(x[1])) & 0xFFFF,
-                "ADD_MUX": (int(x[0]) + int(x[1])) & 0xFFFF}
+                "ADD_MUX": (int(x[0]) + int(x[1])) & 0xFFFF,
+                "MUL_TREE": (int(x[0]) * int(x[1])) & 0xFFFF}
         assert decrypt_word(ce, sk, o1.cpu().numpy().view(np.uint32)[0]) == want[unit]
         return ts
 
     add1_ms = alone_ms("ADD", 30)
     mul1_ms = alone_ms("MUL", 20)
     addmux1_ms = alone_ms("ADD_MUX", 30)   # the same adder, each span's carry one MUX
+    multree1_ms = alone_ms("MUL_TREE", 20)  # the low half by column compression
 
     def batching_leg(pairs):
         """Level batching against one launch per gate (ce_set_level_batching):
@@ -532,6 +534,8 @@ def run_ours(args, rank: int, world: int, local: int):
                                "add16_mux_carry_alone_p50": pct(addmux1_ms, 50),
                                "add16_mux_carry_alone_p99": pct(addmux1_ms, 99),
                                "mul16_alone_p50": pct(mul1_ms, 50),
+                               "mul16_tree_alone_p50": pct(multree1_ms, 50),
+                               "mul16_tree_alone_p99": pct(multree1_ms, 99),
                                "mul16_alone_p99": pct(mul1_ms, 99),
                                "mul16_alone_repeats": len(mul1_ms),
                                "add16_batch256_step_p50": pct(step_ms, 50),

@@ -294,7 +294,11 @@ typedef enum {
     CE_U_ADD_MUX = 18,    /* ADD's parallel-prefix adder (§5 "Adder") with each span
                              combine's carry as one MUX, G = P ? G' : G, instead of
                              AND then OR: the same bootstraps in fewer levels */
-    CE_U_SUB_MUX = 19     /* SUB (§5 "Subtractor") with that adder */
+    CE_U_SUB_MUX = 19,    /* SUB (§5 "Subtractor") with that adder */
+    CE_U_MUL_TREE = 20    /* MUL's low half (§5 "Multiplier") by column compression: full
+                             adders on three bits of a weight per stage (a Wallace
+                             tree), then the MUX-carry adder; more bootstraps, fewer
+                             levels than the array */
 } ce_unit;
 
 /* Shape of a unit's netlist for width w (a power of two, 2..32). */

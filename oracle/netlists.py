@@ -26,7 +26,7 @@ MUX = 10
 OPS = {"NAND": 0, "AND": 1, "OR": 2, "XOR": 3, "NOR": 4, "XNOR": 5, "ANDNY": 6, "ANDYN": 7,
        "ORNY": 8, "ORYN": 9}
 UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "CSEL", "LSR",
-         "ASR", "EOR", "ORN", "ADDS", "SUBS", "SMULL", "UMULL", "ADD_MUX", "SUB_MUX"]
+         "ASR", "EOR", "ORN", "ADDS", "SUBS", "SMULL", "UMULL", "ADD_MUX", "SUB_MUX", "MUL_TREE"]
 CONDS = ["EQ", "NE", "CS", "CC", "MI", "PL", "VS", "VC", "HI", "LS", "GE", "LT", "GT", "LE"]
 
 
@@ -119,6 +119,51 @@ def prefix_adder(net, a, b, carry_in=None, mux_carry=False):
         s0 = net.g("XOR", prop[0], carry_in)
     sums = [s0] + [net.g("XOR", prop[i], G[i - 1]) for i in range(1, w)]
     return sums, G[w - 1]
+
+
+def tree_multiplier(net, a, b):
+    """Low w bits of a * b by column compression: the partial products
+    a_j AND b_i (i + j < w; i outer) fill one heap per weight; while a heap
+    holds more than two bits, each stage replaces, per weight from the
+    lowest, every three bits x, y, z by a full adder (u = x XOR y, sum
+    u XOR z, carry MUX(u; z, x) one weight up) and a remaining pair of a
+    heap taller than two by a half adder (XOR, AND), passing the rest on;
+    a new heap receives the carries from below first, then its sums, then
+    its passed bits; carries out of the top weight are dropped.  From the
+    lowest weight holding two bits up, the two rows are added by the
+    MUX-carry prefix adder (a missing second bit is the constant false)."""
+    w = len(a)
+    heaps = [[] for _ in range(w)]
+    for i in range(w):
+        for j in range(w - i):
+            heaps[i + j].append(net.g("AND", a[j], b[i]))
+    while max(len(h) for h in heaps) > 2:
+        new = [[] for _ in range(w)]
+        for k, h in enumerate(heaps):
+            t = 0
+            while len(h) - t >= 3:
+                x, y, z = h[t:t + 3]
+                t += 3
+                u = net.g("XOR", x, y)
+                new[k].append(net.g("XOR", u, z))
+                if k + 1 < w:
+                    new[k + 1].append(net.mux(u, z, x))
+            if len(h) - t == 2 and len(h) > 2:
+                x, y = h[t:t + 2]
+                t += 2
+                new[k].append(net.g("XOR", x, y))
+                if k + 1 < w:
+                    new[k + 1].append(net.g("AND", x, y))
+            new[k].extend(h[t:])
+        heaps = new
+    two = [k for k in range(w) if len(heaps[k]) == 2]
+    if not two:
+        return [h[0] for h in heaps]
+    k0 = two[0]
+    x = [heaps[k][0] for k in range(k0, w)]
+    y = [heaps[k][1] if len(heaps[k]) == 2 else FALSE for k in range(k0, w)]
+    sums, _ = prefix_adder(net, x, y, mux_carry=True)
+    return [heaps[k][0] for k in range(k0)] + sums
 
 
 def ripple_adder(net, a, b):
@@ -270,6 +315,8 @@ def build(unit: str, w: int = 16, cond: int = 0) -> Net:
                 S[k] = s
             carries = nxt
         out = S
+    elif unit == "MUL_TREE":
+        out = tree_multiplier(net, a, b)
     elif unit == "UDIV":
         A = [FALSE] * (w + 1)
         Q = list(a)
@@ -369,7 +416,7 @@ def armv8(unit: str, a: int, b: int, w: int = 16, cond: int = 0, nzcv: int = 0):
     if unit == "ASR":
         sa = a - (1 << w) if a >> (w - 1) else a
         return (sa >> (b % w)) & m
-    if unit == "MUL":
+    if unit in ("MUL", "MUL_TREE"):
         return (a * b) & m
     if unit == "UMULL":
         return a * b

@@ -403,7 +403,8 @@ def ce_profile_read(ctx: Context) -> dict:
 
 
 UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "CSEL", "LSR",
-         "ASR", "EOR", "ORN", "ADDS", "SUBS", "SMULL", "UMULL", "ADD_MUX", "SUB_MUX"]
+         "ASR", "EOR", "ORN", "ADDS", "SUBS", "SMULL", "UMULL", "ADD_MUX", "SUB_MUX",
+         "MUL_TREE"]
 UNIT_ID = {u: i for i, u in enumerate(UNITS)}
 
 

@@ -177,6 +177,60 @@ Ref condition(Builder &B, int cond, Ref N, Ref Z, Ref C, Ref V) {
   }
 }
 
+// Low w bits of a * b by column compression (a Wallace tree).  The partial
+// products a_j AND b_i (i + j < w, i outer) go to one heap per weight.  While
+// a heap holds more than two bits, a stage walks the weights upward: every
+// three bits x, y, z become a full adder (u = x ^ y; sum u ^ z stays; carry
+// = u ? z : x, one MUX, moves one weight up) and the last pair of a heap that
+// held more than two a half adder (XOR, AND); other bits pass on.  A heap of
+// the next stage holds, in order, the carries from the weight below, its own
+// sums, then its passed bits; carries out of the top weight are dropped.  The
+// two rows left from the lowest weight with two bits up are summed by the
+// MUX-carry prefix adder (a missing second bit: constant false).
+std::vector<Ref> tree_multiplier(Builder &B, const std::vector<Ref> &a, const std::vector<Ref> &b) {
+  const int w = static_cast<int>(a.size());
+  std::vector<std::vector<Ref>> heap(w);
+  for (int i = 0; i < w; ++i)
+    for (int j = 0; j + i < w; ++j) heap[i + j].push_back(B.gate(AND, a[j], b[i]));
+  auto tallest = [&] {
+    size_t m = 0;
+    for (const auto &h : heap) m = std::max(m, h.size());
+    return m;
+  };
+  while (tallest() > 2) {
+    std::vector<std::vector<Ref>> next(w);
+    for (int k = 0; k < w; ++k) {
+      const std::vector<Ref> &h = heap[k];
+      size_t t = 0;
+      for (; h.size() - t >= 3; t += 3) {
+        const Ref u = B.gate(XOR, h[t], h[t + 1]);
+        next[k].push_back(B.gate(XOR, u, h[t + 2]));
+        if (k + 1 < w) next[k + 1].push_back(B.mux(u, h[t + 2], h[t]));
+      }
+      if (h.size() - t == 2 && h.size() > 2) {
+        next[k].push_back(B.gate(XOR, h[t], h[t + 1]));
+        if (k + 1 < w) next[k + 1].push_back(B.gate(AND, h[t], h[t + 1]));
+        t += 2;
+      }
+      for (; t < h.size(); ++t) next[k].push_back(h[t]);
+    }
+    heap = std::move(next);
+  }
+  int k0 = 0;
+  while (k0 < w && heap[k0].size() < 2) ++k0;
+  std::vector<Ref> out(w);
+  for (int k = 0; k < k0; ++k) out[k] = heap[k][0];
+  if (k0 == w) return out;
+  std::vector<Ref> x, y;
+  for (int k = k0; k < w; ++k) {
+    x.push_back(heap[k][0]);
+    y.push_back(heap[k].size() == 2 ? heap[k][1] : constant(false));
+  }
+  const std::vector<Ref> s = kogge_stone(B, x, y, 0, Ref{}, true).sum;
+  for (int k = k0; k < w; ++k) out[k] = s[k - k0];
+  return out;
+}
+
 // Full-width array multiplier: the 2w-bit product of a and b.  Partial
 // products pp[i][j] = a_j AND b_i at weight i + j.  Signed (§5 "Signed
 // multiplication": the partial products' sign extension to 2w bits replaced
@@ -274,6 +328,9 @@ bool build_unit(int unit, int w, int cond, Netlist *out) {
     }
     case kUnitAddMux:
       o = kogge_stone(B, a, b, 0, Ref{}, true).sum;
+      break;
+    case kUnitMulTree:
+      o = tree_multiplier(B, a, b);
       break;
     case kUnitSubMux: {
       std::vector<Ref> nb(w);

@@ -65,7 +65,8 @@ enum Unit : int {
   kUnitUmull = 17,     // unsigned a * b, full 2w-bit product (§5 "Unsigned multiplication")
   kUnitAddMux = 18,    // ADD with each span combine's carry as one MUX (fewer levels)
   kUnitSubMux = 19,    // SUB likewise
-  kUnitCount = 20
+  kUnitMulTree = 20,   // MUL's low half by column compression (a Wallace tree): fewer levels
+  kUnitCount = 21
 };
 
 // Inputs: a[width] then b[width] (CSEL: rn[width], rm[width], N, Z, C, V).

@@ -50,7 +50,7 @@ def operands(rng, n):
 
 
 @pytest.mark.parametrize("unit", ["ADD", "SUB", "AND", "ORR", "LSL", "LSR", "ASR", "MUL", "CMP",
-                                  "ADD_MUX", "SUB_MUX"])
+                                  "ADD_MUX", "SUB_MUX", "MUL_TREE"])
 def test_unit32_semantics(ce, ctx, keys, unit):
     sk, _ = keys
     rng = np.random.default_rng(320 + NL.UNITS.index(unit))

@@ -8,7 +8,7 @@ import pytest
 from oracle import netlists as NL
 
 UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "LSR", "ASR",
-         "EOR", "ORN", "ADDS", "SUBS", "SMULL", "UMULL", "ADD_MUX", "SUB_MUX"]
+         "EOR", "ORN", "ADDS", "SUBS", "SMULL", "UMULL", "ADD_MUX", "SUB_MUX", "MUL_TREE"]
 
 
 def eval_vec(net, inputs):
@@ -216,3 +216,17 @@ def test_mux_carry_adders_keep_the_bootstraps_in_fewer_levels(w):
         assert sum(1 for g in f.gates if g[0] == NL.MUX) == spans
         assert f.depth == 2 + int(math.log2(w))
         assert b.depth > f.depth
+
+
+def test_tree_multiplier_structure():
+    """MUL_TREE: the array multiplier's partial products, compressed by full
+    and half adders until every weight holds at most two bits, then one
+    MUX-carry prefix adder: far fewer levels than the array (whose rows are
+    sequential), at the cost of more bootstraps; the stage count follows the
+    Wallace bound for the tallest column (w bits at weight w - 1)."""
+    for w, depth in ((8, 13), (16, 18), (32, 22)):
+        tree, array = NL.build("MUL_TREE", w), NL.build("MUL", w)
+        assert tree.depth == depth and array.depth == 2 * w - 2
+        assert tree.bootstraps > array.bootstraps
+        ands = [g for g in tree.gates if g[0] == NL.OPS["AND"] and g[5] == 1]
+        assert len(ands) == w * (w + 1) // 2          # the partial products, level 1

@@ -150,7 +150,7 @@ def test_one_launch_per_gate_equals_level_batching(ce, ctx, keys, unit, cond):
     assert per_gate_launches > 10 * batched_launches
 
 
-@pytest.mark.parametrize("unit", ["AND", "LSL", "ADD", "ASR", "ADD_MUX", "SUB_MUX", "MUL_TREE"])
+@pytest.mark.parametrize("unit", ["AND", "LSL", "ADD", "ASR", "ADD_MUX", "SUB_MUX"])
 def test_unit_ciphertexts_match_oracle(ce, ctx, keys, O, full_keys, unit):
     """One instance, every output word equal to the oracle evaluating its own
     (independently built) netlist gate by gate."""

@@ -352,6 +352,13 @@ ce_status ce_set_unit_graphs(ce_ctx *ctx, int on);
  * passage: a measurement mode that sets gate-at-a-time evaluation against
  * the level-batched engine. */
 ce_status ce_set_level_batching(ce_ctx *ctx, int on);
+/* Circuits of the instructions ADD, SUB and MUL in ce_exec*, ce_exec_branching
+ * and the server: 0 (default) the paper's (CE_U_ADD, CE_U_SUB, CE_U_MUL), 1
+ * the low-latency ones with the same semantics (CE_U_ADD_MUX, CE_U_SUB_MUX,
+ * CE_U_MUL_TREE: fewer levels, MUL_TREE with more bootstraps).  Applies to
+ * instructions started later; register results decrypt to the same values,
+ * their ciphertexts differ. */
+ce_status ce_set_instruction_circuits(ce_ctx *ctx, int low_latency);
 
 /* ------------------------------------------- encrypted register programs --- */
 

@@ -68,6 +68,7 @@ def lib() -> ctypes.CDLL:
         "ce_negacyclic_mul_device": (i32, [vp, vp, vp, vp, sz, vp]),
         "ce_set_blind_rotate_config": (i32, [vp, i32, i32]),
         "ce_set_level_batching": (i32, [vp, i32]),
+        "ce_set_instruction_circuits": (i32, [vp, i32]),
         "ce_blind_rotate_plan": (i32, [i32, i32, i32, ctypes.POINTER(i32)]),
         "ce_set_keyswitch_config": (i32, [vp, i32]),
         "ce_set_external_product_form": (i32, [vp, i32]),
@@ -319,6 +320,13 @@ def ce_blind_rotate_plan(n_jobs: int, gates_per_block: int, blocks: int) -> dict
     _check(lib().ce_blind_rotate_plan(n_jobs, gates_per_block, blocks, out),
            "ce_blind_rotate_plan")
     return {"main_jobs": out[0], "tail_jobs": out[1], "tail_shape": out[2], "tail_blocks": out[3]}
+
+
+def ce_set_instruction_circuits(ctx: Context, low_latency: bool):
+    """False: ADD / SUB / MUL instructions on the paper's circuits (default);
+    True: on ADD_MUX / SUB_MUX / MUL_TREE (same semantics, fewer levels)."""
+    _check(lib().ce_set_instruction_circuits(ctx.ptr, 1 if low_latency else 0),
+           "ce_set_instruction_circuits")
 
 
 def ce_set_level_batching(ctx: Context, on: bool):

@@ -66,6 +66,7 @@ struct ce_ctx {
   int cfg_g = 0, cfg_bps = 0;
   int cfg_ks = 0;  // key switch: 0 automatic, 1 CUDA cores, 2 tensor cores
   bool per_gate = false;  // engine levels as one launch per gate and step (comparison mode)
+  bool fast_circuits = false;  // instructions ADD / SUB / MUL on ADD_MUX / SUB_MUX / MUL_TREE
   int cfg_xp = 0;  // external product: 0 transform (CUDA cores), 1 Toeplitz (tensor cores)
   uint16_t *tt_digits = nullptr;  // digit operand of the tensor-core external product
   size_t tt_cap = 0;              // jobs the digit operand holds

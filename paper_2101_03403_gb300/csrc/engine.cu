@@ -183,6 +183,7 @@ constexpr int kRegBits = kRegs * kWidth + 4;  // 8 x 16 register bits + NZCV
 struct ProgPlan {
   int xp = 0, ks = 0;                       // external-product form, key-switch engine
   bool per_gate = false;                    // one launch per gate and step
+  bool fast_circuits = false;               // ADD / SUB / MUL on the low-latency circuits
   std::vector<int> clients;                 // per program
   std::vector<std::vector<uint8_t>> code;   // per program: instruction bytes
   std::vector<int> regfiles;                // distinct clients, in first-use order
@@ -920,7 +921,15 @@ bool wire_move(const ce_insn &I, const SRef *rd, const SRef *rn, int j, SRef *ou
   }
 }
 
-int unit_of(uint8_t op) {
+// The unit an instruction runs; with low-latency circuits selected, ADD, SUB
+// and MUL run the same operations on the MUX-carry adders and the tree
+// multiplier (fewer levels).
+int unit_of(uint8_t op, bool low_latency) {
+  if (low_latency) {
+    if (op == kAdd) return kUnitAddMux;
+    if (op == kSub) return kUnitSubMux;
+    if (op == kMul) return kUnitMulTree;
+  }
   switch (op) {
     case kAdd: return kUnitAdd;
     case kSub: return kUnitSub;
@@ -980,7 +989,7 @@ ce_status advance(Engine &E, Run &r) {
       ++r.pc;
       continue;
     }
-    const Netlist *net = E.netlist(unit_of(I.op), I.cond);
+    const Netlist *net = E.netlist(unit_of(I.op, E.ctx->fast_circuits), I.cond);
     std::vector<SRef> in;
     for (int j = 0; j < kWidth; ++j) in.push_back(R.r[I.rn][j]);
     for (int j = 0; j < kWidth; ++j) in.push_back(R.r[I.rm][j]);
@@ -1019,7 +1028,7 @@ void retire(Engine &E, Run &r) {
 bool plan_matches(const ce_ctx *ctx, const ProgPlan &p, size_t n_prog, const int *clients,
                   const ce_insn *const *progs, const size_t *lens) {
   if (p.clients.size() != n_prog || p.xp != ctx->cfg_xp || p.ks != ctx->cfg_ks ||
-      p.per_gate != ctx->per_gate)
+      p.per_gate != ctx->per_gate || p.fast_circuits != ctx->fast_circuits)
     return false;
   for (size_t i = 0; i < n_prog; ++i) {
     if (p.clients[i] != clients[i] || p.code[i].size() != lens[i] * sizeof(ce_insn)) return false;
@@ -1038,6 +1047,7 @@ ce_status make_prog_plan(Engine &E, size_t n_prog, const int *clients, const ce_
   p->xp = E.ctx->cfg_xp;
   p->ks = E.ctx->cfg_ks;
   p->per_gate = E.ctx->per_gate;
+  p->fast_circuits = E.ctx->fast_circuits;
   for (size_t i = 0; i < n_prog; ++i) {
     p->clients.push_back(clients[i]);
     const uint8_t *b = reinterpret_cast<const uint8_t *>(progs[i]);
@@ -1455,6 +1465,13 @@ extern "C" ce_status ce_unit_eval_device(ce_ctx *ctx, int client, int unit, int 
                                          const uint32_t *d_in, uint32_t *d_out, size_t n,
                                          void *cuda_stream) {
   return ce_unit_eval_device_width(ctx, client, unit, cond, 16, d_in, d_out, n, cuda_stream);
+}
+
+extern "C" ce_status ce_set_instruction_circuits(ce_ctx *ctx, int low_latency) {
+  if (!ctx) return set_error(CE_EINVAL, "ce_set_instruction_circuits: null context");
+  std::lock_guard<std::recursive_mutex> ctx_lock(ctx->mu);
+  ctx->fast_circuits = low_latency != 0;
+  return CE_OK;
 }
 
 extern "C" ce_status ce_set_level_batching(ce_ctx *ctx, int on) {

@@ -135,6 +135,28 @@ def test_every_instruction(ce, ctx, keys):
     assert flags == [(exp_nzcv >> k) & 1 for k in range(4)]
 
 
+def test_low_latency_instruction_circuits(ce, ctx, keys):
+    """ADD, SUB and MUL on the MUX-carry adders and the tree multiplier
+    (ce_set_instruction_circuits): the plaintext machine's registers, with
+    the program set planned and replayed as a graph and run eagerly."""
+    c, cid = ctx
+    sk, _ = keys
+    init = [1234, 56, 0xFFFF, 7, 65535, 3, 0x8000, 9]
+    prog = [("ADD", 2, 0, 1, 0, 0), ("SUB", 3, 1, 0, 0, 0), ("MUL", 5, 0, 1, 0, 0),
+            ("ADD", 6, 4, 6, 0, 0), ("MUL", 7, 2, 3, 0, 0), ("SUB", 1, 7, 2, 0, 0)]
+    exp = run_plain(prog, init)[0]
+    ce.ce_set_instruction_circuits(c, True)
+    try:
+        for graphs in (True, False):
+            ce.ce_set_unit_graphs(c, graphs)
+            load_regs(ce, c, cid, sk, init, 44)
+            ce.ce_exec(c, cid, [ce.insn(*i) for i in prog])
+            assert read_regs(ce, c, cid, sk) == exp
+    finally:
+        ce.ce_set_unit_graphs(c, True)
+        ce.ce_set_instruction_circuits(c, False)
+
+
 def test_mul_udiv_program(ce, ctx, keys):
     c, cid = ctx
     sk, _ = keys

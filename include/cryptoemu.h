@@ -295,10 +295,12 @@ typedef enum {
                              combine's carry as one MUX, G = P ? G' : G, instead of
                              AND then OR: the same bootstraps in fewer levels */
     CE_U_SUB_MUX = 19,    /* SUB (§5 "Subtractor") with that adder */
-    CE_U_MUL_TREE = 20    /* MUL's low half (§5 "Multiplier") by column compression: full
+    CE_U_MUL_TREE = 20,   /* MUL's low half (§5 "Multiplier") by column compression: full
                              adders on three bits of a weight per stage (a Wallace
                              tree), then the MUX-carry adder; more bootstraps, fewer
                              levels than the array */
+    CE_U_UDIV_MUX = 21    /* UDIV (§5 "Divider") with the MUX-carry adder in every
+                             step (its encrypted carry-in folded in by a MUX too) */
 } ce_unit;
 
 /* Shape of a unit's netlist for width w (a power of two, 2..32). */
@@ -352,10 +354,11 @@ ce_status ce_set_unit_graphs(ce_ctx *ctx, int on);
  * passage: a measurement mode that sets gate-at-a-time evaluation against
  * the level-batched engine. */
 ce_status ce_set_level_batching(ce_ctx *ctx, int on);
-/* Circuits of the instructions ADD, SUB and MUL in ce_exec*, ce_exec_branching
- * and the server: 0 (default) the paper's (CE_U_ADD, CE_U_SUB, CE_U_MUL), 1
- * the low-latency ones with the same semantics (CE_U_ADD_MUX, CE_U_SUB_MUX,
- * CE_U_MUL_TREE: fewer levels, MUL_TREE with more bootstraps).  Applies to
+/* Circuits of the instructions ADD, SUB, MUL and UDIV in ce_exec*,
+ * ce_exec_branching and the server: 0 (default) the paper's (CE_U_ADD,
+ * CE_U_SUB, CE_U_MUL, CE_U_UDIV), 1 the low-latency ones with the same
+ * semantics (CE_U_ADD_MUX, CE_U_SUB_MUX, CE_U_MUL_TREE, CE_U_UDIV_MUX: fewer
+ * levels, MUL_TREE with more bootstraps).  Applies to
  * instructions started later; register results decrypt to the same values,
  * their ciphertexts differ. */
 ce_status ce_set_instruction_circuits(ce_ctx *ctx, int low_latency);

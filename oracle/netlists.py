@@ -26,7 +26,8 @@ MUX = 10
 OPS = {"NAND": 0, "AND": 1, "OR": 2, "XOR": 3, "NOR": 4, "XNOR": 5, "ANDNY": 6, "ANDYN": 7,
        "ORNY": 8, "ORYN": 9}
 UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "CSEL", "LSR",
-         "ASR", "EOR", "ORN", "ADDS", "SUBS", "SMULL", "UMULL", "ADD_MUX", "SUB_MUX", "MUL_TREE"]
+         "ASR", "EOR", "ORN", "ADDS", "SUBS", "SMULL", "UMULL", "ADD_MUX", "SUB_MUX", "MUL_TREE",
+         "UDIV_MUX"]
 CONDS = ["EQ", "NE", "CS", "CC", "MI", "PL", "VS", "VC", "HI", "LS", "GE", "LT", "GT", "LE"]
 
 
@@ -85,7 +86,8 @@ def prefix_adder(net, a, b, carry_in=None, mux_carry=False):
     subtractor's constant 1) or an encrypted wire.  mux_carry: the combined
     G of a span is MUX(P_i; G_{i-d}, G_i) — a span whose bits all propagate
     generates nothing itself, so this equals G_i OR (P_i AND G_{i-d}) — built
-    before the AND of the P's."""
+    before the AND of the P's; an encrypted carry-in c gives G_0 =
+    MUX(p_0; c, g_0) likewise."""
     w = len(a)
     gen, prop = [], []
     for i in range(w):
@@ -94,6 +96,8 @@ def prefix_adder(net, a, b, carry_in=None, mux_carry=False):
     G, P = list(gen), list(prop)
     if carry_in == "one":
         G[0] = net.g("OR", gen[0], prop[0])
+    elif carry_in is not None and mux_carry:
+        G[0] = net.mux(prop[0], carry_in, gen[0])
     elif carry_in is not None:
         t = net.g("AND", prop[0], carry_in)
         G[0] = net.g("OR", gen[0], t)
@@ -317,7 +321,7 @@ def build(unit: str, w: int = 16, cond: int = 0) -> Net:
         out = S
     elif unit == "MUL_TREE":
         out = tree_multiplier(net, a, b)
-    elif unit == "UDIV":
+    elif unit in ("UDIV", "UDIV_MUX"):
         A = [FALSE] * (w + 1)
         Q = list(a)
         for _ in range(w):
@@ -326,7 +330,7 @@ def build(unit: str, w: int = 16, cond: int = 0) -> Net:
             Q = [None] + Q[:w - 1]
             sub = neg(sign)                        # subtract while A >= 0
             dx = [net.g("XOR", b[k], sub) for k in range(w)] + [sub]
-            A, _ = prefix_adder(net, shifted, dx, sub)
+            A, _ = prefix_adder(net, shifted, dx, sub, mux_carry=unit == "UDIV_MUX")
             Q[0] = neg(A[w])
         nonzero = or_reduce(net, b)
         out = [net.g("AND", Q[k], nonzero) for k in range(w)]
@@ -424,7 +428,7 @@ def armv8(unit: str, a: int, b: int, w: int = 16, cond: int = 0, nzcv: int = 0):
         sa = a - (1 << w) if a >> (w - 1) else a
         sb = b - (1 << w) if b >> (w - 1) else b
         return (sa * sb) & ((1 << 2 * w) - 1)
-    if unit == "UDIV":
+    if unit in ("UDIV", "UDIV_MUX"):
         return 0 if b == 0 else a // b
     if unit == "CMP":
         r = (a - b) & m

@@ -323,8 +323,9 @@ def ce_blind_rotate_plan(n_jobs: int, gates_per_block: int, blocks: int) -> dict
 
 
 def ce_set_instruction_circuits(ctx: Context, low_latency: bool):
-    """False: ADD / SUB / MUL instructions on the paper's circuits (default);
-    True: on ADD_MUX / SUB_MUX / MUL_TREE (same semantics, fewer levels)."""
+    """False: ADD / SUB / MUL / UDIV instructions on the paper's circuits
+    (default); True: on ADD_MUX / SUB_MUX / MUL_TREE / UDIV_MUX (same
+    semantics, fewer levels)."""
     _check(lib().ce_set_instruction_circuits(ctx.ptr, 1 if low_latency else 0),
            "ce_set_instruction_circuits")
 
@@ -412,7 +413,7 @@ def ce_profile_read(ctx: Context) -> dict:
 
 UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "CSEL", "LSR",
          "ASR", "EOR", "ORN", "ADDS", "SUBS", "SMULL", "UMULL", "ADD_MUX", "SUB_MUX",
-         "MUL_TREE"]
+         "MUL_TREE", "UDIV_MUX"]
 UNIT_ID = {u: i for i, u in enumerate(UNITS)}
 
 

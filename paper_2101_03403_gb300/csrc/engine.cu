@@ -921,14 +921,15 @@ bool wire_move(const ce_insn &I, const SRef *rd, const SRef *rn, int j, SRef *ou
   }
 }
 
-// The unit an instruction runs; with low-latency circuits selected, ADD, SUB
-// and MUL run the same operations on the MUX-carry adders and the tree
+// The unit an instruction runs; with low-latency circuits selected, ADD, SUB,
+// MUL and UDIV run the same operations on the MUX-carry adders and the tree
 // multiplier (fewer levels).
 int unit_of(uint8_t op, bool low_latency) {
   if (low_latency) {
     if (op == kAdd) return kUnitAddMux;
     if (op == kSub) return kUnitSubMux;
     if (op == kMul) return kUnitMulTree;
+    if (op == kUdiv) return kUnitUdivMux;
   }
   switch (op) {
     case kAdd: return kUnitAdd;

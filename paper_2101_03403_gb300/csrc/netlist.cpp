@@ -71,7 +71,8 @@ struct AdderOut {
 // mux_prefix: the span combine's G as one MUX, G_i <- P_i ? G_{i-d} : G_i
 // (equal to G_i OR (P_i AND G_{i-d}) because a span that propagates
 // generates nothing of its own), created before P's AND: the same
-// bootstraps in one level per span instead of two.
+// bootstraps in one level per span instead of two; likewise an encrypted
+// carry-in folds in as G_0 = p_0 ? c : g_0.
 AdderOut kogge_stone(Builder &B, const std::vector<Ref> &a, const std::vector<Ref> &b,
                      int cin_kind, Ref cin, bool mux_prefix = false) {
   const int w = static_cast<int>(a.size());
@@ -83,6 +84,8 @@ AdderOut kogge_stone(Builder &B, const std::vector<Ref> &a, const std::vector<Re
   std::vector<Ref> G = g, P = p;
   if (cin_kind == 1) {
     G[0] = B.gate(OR, g[0], p[0]);
+  } else if (cin_kind == 2 && mux_prefix) {
+    G[0] = B.mux(p[0], cin, g[0]);
   } else if (cin_kind == 2) {
     const Ref t = B.gate(AND, p[0], cin);
     G[0] = B.gate(OR, g[0], t);
@@ -414,7 +417,8 @@ bool build_unit(int unit, int w, int cond, Netlist *out) {
       o = S;
       break;
     }
-    case kUnitUdiv: {
+    case kUnitUdiv:
+    case kUnitUdivMux: {
       // Non-restoring division (§5 "Divider") with a (w+1)-bit partial
       // remainder A (two's complement, sign A_w) and D = b extended by a
       // zero bit.  Per iteration: sgn = A_w before the shift; [A, Q] <<= 1;
@@ -432,7 +436,7 @@ bool build_unit(int unit, int w, int cond, Netlist *out) {
         std::vector<Ref> Dx(w + 1);
         for (int k = 0; k < w; ++k) Dx[k] = B.gate(XOR, b[k], sub);
         Dx[w] = sub;
-        A = kogge_stone(B, As, Dx, 2, sub).sum;
+        A = kogge_stone(B, As, Dx, 2, sub, unit == kUnitUdivMux).sum;
         Q[0] = !A[w];
       }
       const Ref nz = or_tree(B, b);

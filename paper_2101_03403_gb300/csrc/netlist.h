@@ -66,7 +66,8 @@ enum Unit : int {
   kUnitAddMux = 18,    // ADD with each span combine's carry as one MUX (fewer levels)
   kUnitSubMux = 19,    // SUB likewise
   kUnitMulTree = 20,   // MUL's low half by column compression (a Wallace tree): fewer levels
-  kUnitCount = 21
+  kUnitUdivMux = 21,   // UDIV with the MUX-carry adder in every step
+  kUnitCount = 22
 };
 
 // Inputs: a[width] then b[width] (CSEL: rn[width], rm[width], N, Z, C, V).

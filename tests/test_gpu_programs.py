@@ -136,14 +136,16 @@ def test_every_instruction(ce, ctx, keys):
 
 
 def test_low_latency_instruction_circuits(ce, ctx, keys):
-    """ADD, SUB and MUL on the MUX-carry adders and the tree multiplier
-    (ce_set_instruction_circuits): the plaintext machine's registers, with
-    the program set planned and replayed as a graph and run eagerly."""
+    """ADD, SUB, MUL and UDIV on the MUX-carry adders and the tree
+    multiplier (ce_set_instruction_circuits): the plaintext machine's
+    registers, with the program set planned and replayed as a graph and run
+    eagerly."""
     c, cid = ctx
     sk, _ = keys
     init = [1234, 56, 0xFFFF, 7, 65535, 3, 0x8000, 9]
     prog = [("ADD", 2, 0, 1, 0, 0), ("SUB", 3, 1, 0, 0, 0), ("MUL", 5, 0, 1, 0, 0),
-            ("ADD", 6, 4, 6, 0, 0), ("MUL", 7, 2, 3, 0, 0), ("SUB", 1, 7, 2, 0, 0)]
+            ("ADD", 6, 4, 6, 0, 0), ("MUL", 7, 2, 3, 0, 0), ("SUB", 1, 7, 2, 0, 0),
+            ("UDIV", 4, 4, 1, 0, 0)]
     exp = run_plain(prog, init)[0]
     ce.ce_set_instruction_circuits(c, True)
     try:

@@ -77,17 +77,18 @@ def test_unit_semantics(ce, ctx, keys, unit):
         assert got == exp, (unit, int(a[i]), int(b[i]), got, exp)
 
 
-def test_udiv_semantics(ce, ctx, keys):
+@pytest.mark.parametrize("unit", ["UDIV", "UDIV_MUX"])
+def test_udiv_semantics(ce, ctx, keys, unit):
     sk, _ = keys
     rng = np.random.default_rng(9)
     n = 12
     a, b = operands(rng, n)
     b[4] = 1
     b[5] = rng.integers(1, 16)
-    out = run_unit(ce, ctx, "UDIV", enc_operands(ce, sk, operand_bits(a, b), 6), W)
+    out = run_unit(ce, ctx, unit, enc_operands(ce, sk, operand_bits(a, b), 6), W)
     bits = decrypt_all(ce, sk, out)
     for i in range(n):
-        assert NL.from_bits(bits[i]) == NL.armv8("UDIV", int(a[i]), int(b[i]), W)
+        assert NL.from_bits(bits[i]) == NL.armv8(unit, int(a[i]), int(b[i]), W)
 
 
 @pytest.mark.parametrize("cond", [0, 8, 10, 12])

@@ -8,7 +8,8 @@ import pytest
 from oracle import netlists as NL
 
 UNITS = ["ADD", "ADD_RIPPLE", "SUB", "AND", "ORR", "LSL", "MUL", "UDIV", "CMP", "LSR", "ASR",
-         "EOR", "ORN", "ADDS", "SUBS", "SMULL", "UMULL", "ADD_MUX", "SUB_MUX", "MUL_TREE"]
+         "EOR", "ORN", "ADDS", "SUBS", "SMULL", "UMULL", "ADD_MUX", "SUB_MUX", "MUL_TREE",
+         "UDIV_MUX"]
 
 
 def eval_vec(net, inputs):
@@ -82,14 +83,14 @@ def test_random_width16(unit):
 @pytest.mark.parametrize("unit", UNITS)
 def test_random_width32(unit):
     rng = np.random.default_rng(32)
-    n = 600 if unit == "UDIV" else 2000
+    n = 600 if unit.startswith("UDIV") else 2000
     a = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.int64)
     b = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.int64)
     b[:20] = 0
     b[20:40] = a[20:40]
     a[40:60] = 0xFFFFFFFF
     b[60:120] = rng.integers(0, 64, 60)           # every shift amount mod 32
-    if unit == "UDIV":
+    if unit.startswith("UDIV"):
         b[120:200] = rng.integers(1, 1 << 16, 80)  # quotients of every size
     check_unit(unit, 32, a, b)
 

@@ -51,6 +51,10 @@ def test_bad_arguments_are_errors_not_crashes(L):
         L.ce_cloud_keygen(L.SecretKey(0, 0), 1)
     with pytest.raises(L.CeError):   # no GPU here or bad device: an error code, not an abort
         L.ce_create(device=9999)
+    # option setters: a null context is an error code
+    for fn in ("ce_set_level_batching", "ce_set_instruction_circuits", "ce_set_unit_graphs",
+               "ce_set_external_product_form", "ce_set_keyswitch_config"):
+        assert getattr(L.lib(), fn)(None, 1) != 0, fn
 
 
 def test_blind_rotation_launch_plan(L):
